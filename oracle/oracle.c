@@ -1,0 +1,285 @@
+/*
+ * oracle.c -- plain FP64 CPU reference for ApplyFilter.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline leg call this code.  It shares no code with the CUDA library and includes
+ * none of its headers.
+ *
+ * What is computed (Sec. 3.2, "Volume Manipulation"): ApplyFilter applies a
+ * user-specified convolution kernel (edge detection, Gaussian blur) to a structured
+ * volume, with the same result as the per-cell formulation through Transform.  The
+ * paper fixes no boundary rule, no anchor and no index order, so this file takes these
+ * readings:
+ *   - correlation form, anchor at the kernel centre r = (k-1)/2, k odd:
+ *       y(x,y,z) = sum_{a,b,c in [-r,r]} w[c+r][b+r][a+r] * v(X(x+a), Y(y+b), Z(z+c))
+ *   - clamp-to-edge boundary: X(i) = min(max(i,0), nx-1), same for Y and Z;
+ *   - memory order x fastest, then y, then z (dims order of the create call, Fig.
+ *     exampleCvsCPP); weights stored the same way, a fastest;
+ *   - value mapping of a stored voxel q (Sec. 3.2, create call with format and range):
+ *       uint8/uint16: v = lo + (hi - lo) * q / (2^N - 1);   float32: v = q;
+ *   - quantisation to an integer destination:
+ *       t = (v - lo)/(hi - lo) * (2^N - 1),  q = clamp(round-half-even(t), 0, 2^N - 1).
+ * Everything is evaluated in double precision, one voxel at a time, taps in order.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+#include <fenv.h>
+
+enum { OR_U8 = 0, OR_U16 = 1, OR_F32 = 2 };
+
+static int64_t clampi(int64_t i, int64_t n)
+{
+    return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+/* value of stored voxel number i under the volume's mapping range [lo,hi] */
+static double mapped(const void* src, int fmt, int64_t i, double lo, double hi)
+{
+    switch (fmt) {
+    case OR_U8:  return lo + (hi - lo) * (double)((const uint8_t*)src)[i] / 255.0;
+    case OR_U16: return lo + (hi - lo) * (double)((const uint16_t*)src)[i] / 65535.0;
+    default:     return (double)((const float*)src)[i];
+    }
+}
+
+static int check_args(int fmt, int64_t nx, int64_t ny, int64_t nz, int k)
+{
+    if (fmt < OR_U8 || fmt > OR_F32) return -1;
+    if (nx < 0 || ny < 0 || nz < 0) return -1;
+    if (k < 1 || (k & 1) == 0) return -1;
+    return 0;
+}
+
+/* one output voxel, straight from the definition above */
+static double correlate_at(const void* src, int fmt, double lo, double hi,
+                           int64_t nx, int64_t ny, int64_t nz, const double* w, int k,
+                           int64_t x, int64_t y, int64_t z)
+{
+    int r = (k - 1) / 2;
+    double acc = 0.0;
+    for (int c = 0; c < k; ++c) {
+        int64_t zz = clampi(z + c - r, nz);
+        for (int b = 0; b < k; ++b) {
+            int64_t yy = clampi(y + b - r, ny);
+            for (int a = 0; a < k; ++a) {
+                int64_t xx = clampi(x + a - r, nx);
+                acc += w[((int64_t)c * k + b) * k + a] *
+                       mapped(src, fmt, (zz * ny + yy) * nx + xx, lo, hi);
+            }
+        }
+    }
+    return acc;
+}
+
+/* full volume: out[(z*ny + y)*nx + x] = y(x,y,z) as a double */
+int oracle_correlate(const void* src, int fmt, double lo, double hi,
+                     int64_t nx, int64_t ny, int64_t nz, const double* w, int k,
+                     double* out)
+{
+    if (check_args(fmt, nx, ny, nz, k)) return -1;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x)
+                out[(z * ny + y) * nx + x] =
+                    correlate_at(src, fmt, lo, hi, nx, ny, nz, w, k, x, y, z);
+    return 0;
+}
+
+/* selected voxels only (linear indices), for checks at sizes the full loop cannot reach */
+int oracle_correlate_points(const void* src, int fmt, double lo, double hi,
+                            int64_t nx, int64_t ny, int64_t nz, const double* w, int k,
+                            const int64_t* idx, int64_t npts, double* out)
+{
+    if (check_args(fmt, nx, ny, nz, k)) return -1;
+    int64_t nvox = nx * ny * nz;
+    for (int64_t p = 0; p < npts; ++p)
+        if (idx[p] < 0 || idx[p] >= nvox) return -2;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < npts; ++p) {
+        int64_t i = idx[p];
+        int64_t x = i % nx, y = (i / nx) % ny, z = i / (nx * ny);
+        out[p] = correlate_at(src, fmt, lo, hi, nx, ny, nz, w, k, x, y, z);
+    }
+    return 0;
+}
+
+/*
+ * Quantisation of filtered values to an integer destination with range [lo,hi]
+ * (bits = 8 or 16).  t[i] receives the pre-rounding code value, q[i] the code, and
+ * tie[i] = 1 where t lies within `window` of a half-integer (there either neighbour is
+ * accepted, since no precision short of exact arithmetic decides it).
+ */
+int oracle_quantize(const double* v, int64_t n, int bits, double lo, double hi,
+                    double window, double* t, uint32_t* q, uint8_t* tie)
+{
+    if ((bits != 8 && bits != 16) || !(hi != lo)) return -1;
+    double qmax = (double)((1u << bits) - 1u);
+    int old = fegetround();
+    fesetround(FE_TONEAREST);
+    for (int64_t i = 0; i < n; ++i) {
+        double ti = (v[i] - lo) / (hi - lo) * qmax;
+        double qi = ti != ti ? 0.0 : nearbyint(ti);   /* NaN reads as 0 */
+        qi = qi < 0.0 ? 0.0 : (qi > qmax ? qmax : qi);
+        t[i] = ti;
+        q[i] = (uint32_t)qi;
+        tie[i] = (uint8_t)(fabs(ti - floor(ti) - 0.5) < window);
+    }
+    fesetround(old);
+    return 0;
+}
+
+/*
+ * Filter construction (Gaussian blur, Sec. 1 teaser and Sec. 4.3).  The paper gives
+ * neither size nor sigma, and no definition beyond "Gaussian blur"; the reading taken:
+ * the sampled Gaussian g(d) = exp(-d^2 / (2 sigma^2)) at the integer offsets
+ * d in [-r, r], divided by its sum (FP64), stored as float32.  The 3-D kernel is the
+ * product g[c]*g[b]*g[a] of the stored 1-D weights (the sampled 3-D Gaussian factorises
+ * exactly, so this is the sampled 3-D Gaussian normalised to sum 1).
+ */
+int oracle_gaussian_1d(int k, double sigma, float* g)
+{
+    if (k < 1 || (k & 1) == 0 || !(sigma > 0.0)) return -1;
+    int r = (k - 1) / 2;
+    double e[64], s = 0.0;
+    if (k > 63) return -1;
+    for (int i = 0; i < k; ++i) {
+        double d = (double)(i - r);
+        e[i] = exp(-d * d / (2.0 * sigma * sigma));
+        s += e[i];
+    }
+    for (int i = 0; i < k; ++i) g[i] = (float)(e[i] / s);
+    return 0;
+}
+
+/* dense k^3 weights (double) of a separable filter: w[c][b][a] = gz[c] * gy[b] * gx[a] */
+void oracle_separable_weights(int k, const float* gx, const float* gy, const float* gz,
+                              double* w)
+{
+    for (int c = 0; c < k; ++c)
+        for (int b = 0; b < k; ++b)
+            for (int a = 0; a < k; ++a)
+                w[((int64_t)c * k + b) * k + a] = (double)gz[c] * (double)gy[b] * (double)gx[a];
+}
+
+/*
+ * Gradients of the float32 filter y = C_w x (x float-valued, identity mapping), for a
+ * loss L with dL/dy = gy.  Straight from the definition of y above:
+ *   gx[j] = sum_i sum_d w[d] gy[i] [clamp(i+d) == j]      (adjoint, scatter form)
+ *   gw[d] = sum_i gy[i] x[clamp(i+d)]
+ * The scatter is serial: each input voxel receives from every tap whose clamped
+ * position lands on it, which at a face includes several taps of the same output.
+ */
+int oracle_correlate_backward(const double* x, const double* gy, int64_t nx, int64_t ny,
+                              int64_t nz, const double* w, int k, double* gx, double* gw)
+{
+    if (check_args(OR_F32, nx, ny, nz, k)) return -1;
+    int r = (k - 1) / 2;
+    int64_t n = nx * ny * nz;
+    if (gx) {
+        memset(gx, 0, sizeof(double) * (size_t)n);
+        for (int64_t z = 0; z < nz; ++z)
+            for (int64_t y = 0; y < ny; ++y)
+                for (int64_t xx = 0; xx < nx; ++xx) {
+                    double g = gy[(z * ny + y) * nx + xx];
+                    for (int c = 0; c < k; ++c) {
+                        int64_t sz = clampi(z + c - r, nz);
+                        for (int b = 0; b < k; ++b) {
+                            int64_t sy = clampi(y + b - r, ny);
+                            for (int a = 0; a < k; ++a) {
+                                int64_t sx = clampi(xx + a - r, nx);
+                                gx[(sz * ny + sy) * nx + sx] += w[((int64_t)c * k + b) * k + a] * g;
+                            }
+                        }
+                    }
+                }
+    }
+    if (gw) {
+        int64_t kk = (int64_t)k * k * k;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t d = 0; d < kk; ++d) {
+            int a = (int)(d % k), b = (int)((d / k) % k), c = (int)(d / ((int64_t)k * k));
+            double acc = 0.0;
+            for (int64_t z = 0; z < nz; ++z) {
+                int64_t sz = clampi(z + c - r, nz);
+                for (int64_t y = 0; y < ny; ++y) {
+                    int64_t sy = clampi(y + b - r, ny);
+                    for (int64_t xx = 0; xx < nx; ++xx) {
+                        int64_t sx = clampi(xx + a - r, nx);
+                        acc += gy[(z * ny + y) * nx + xx] * x[(sz * ny + sy) * nx + sx];
+                    }
+                }
+            }
+            gw[d] = acc;
+        }
+    }
+    return 0;
+}
+
+/*
+ * gx at selected voxels j, from the same definition: the outputs i that reach j through
+ * tap d are those whose clamped position i+d equals j on every axis.  Per axis (n > 1):
+ * j interior -> i = j - d (if in range); j = 0 -> every i with i + d <= 0;
+ * j = n-1 -> every i with i + d >= n-1.  (n = 1: every i, i.e. i = 0.)
+ */
+static void axis_sources(int64_t j, int d, int64_t n, int64_t* i0, int64_t* i1)
+{
+    int64_t lo, hi;
+    if (n == 1) { lo = 0; hi = 0; }
+    else if (j == 0) { lo = 0; hi = -d; }
+    else if (j == n - 1) { lo = n - 1 - d; hi = n - 1; }
+    else { lo = j - d; hi = j - d; }
+    if (lo < 0) lo = 0;
+    if (hi > n - 1) hi = n - 1;
+    *i0 = lo;
+    *i1 = hi;   /* empty when lo > hi */
+}
+
+int oracle_backward_input_points(const double* gy, int64_t nx, int64_t ny, int64_t nz,
+                                 const double* w, int k, const int64_t* idx, int64_t npts,
+                                 double* out)
+{
+    if (check_args(OR_F32, nx, ny, nz, k)) return -1;
+    int r = (k - 1) / 2;
+    int64_t nvox = nx * ny * nz;
+    for (int64_t p = 0; p < npts; ++p)
+        if (idx[p] < 0 || idx[p] >= nvox) return -2;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < npts; ++p) {
+        int64_t j = idx[p];
+        int64_t jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+        double acc = 0.0;
+        for (int c = 0; c < k; ++c) {
+            int64_t z0, z1;
+            axis_sources(jz, c - r, nz, &z0, &z1);
+            for (int b = 0; b < k; ++b) {
+                int64_t y0, y1;
+                axis_sources(jy, b - r, ny, &y0, &y1);
+                for (int a = 0; a < k; ++a) {
+                    int64_t x0, x1;
+                    axis_sources(jx, a - r, nx, &x0, &x1);
+                    double wd = w[((int64_t)c * k + b) * k + a];
+                    for (int64_t z = z0; z <= z1; ++z)
+                        for (int64_t y = y0; y <= y1; ++y)
+                            for (int64_t x = x0; x <= x1; ++x)
+                                acc += wd * gy[(z * ny + y) * nx + x];
+                }
+            }
+        }
+        out[p] = acc;
+    }
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

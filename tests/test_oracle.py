@@ -1,0 +1,349 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each check is chosen so that a plausible slip in the oracle (a dropped tap, a flipped
+kernel, a wrong anchor, zero padding instead of clamping, a wrong mapping, a transposed
+axis, a missing boundary fold in the adjoint) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rnd_vol(seed, shape, lo=-1.0, hi=1.0):
+    return synth.uniform(seed, shape, lo, hi)
+
+
+def rnd_w(seed, k):
+    return synth.normal(seed, (k, k, k), 0.0, 1.0).astype(np.float64)
+
+
+# ---------------------------------------------------------------------- identity, constant
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_identity_kernel_reproduces_input(k):
+    x = rnd_vol(1, (5, 6, 7))
+    w = np.zeros((k, k, k))
+    w[k // 2, k // 2, k // 2] = 1.0
+    y = oracle.correlate(x, w)
+    assert np.array_equal(y, x.astype(np.float64))
+
+
+@pytest.mark.parametrize("fmt,bits", [(synth.U8, 8), (synth.U16, 16)])
+def test_identity_kernel_integer_mapping(fmt, bits):
+    q = (synth.uniform(2, (4, 5, 6)) * (2 ** bits - 1)).astype(synth.NP_DTYPE[fmt])
+    q.flat[0] = 0
+    q.flat[1] = 2 ** bits - 1
+    w = np.zeros((3, 3, 3))
+    w[1, 1, 1] = 1.0
+    lo, hi = -2.0, 6.0
+    y = oracle.correlate(q, w, lo, hi)
+    expect = lo + (hi - lo) * q.astype(np.float64) / (2 ** bits - 1)
+    assert np.allclose(y, expect, rtol=0, atol=1e-15)
+    assert y.flat[0] == lo and y.flat[1] == hi     # code 0 <-> lo, max code <-> hi
+
+
+def test_constant_volume():
+    c = 0.7314
+    x = np.full((6, 5, 9), c, np.float32)
+    g = oracle.gaussian_weights(5, 1.5)
+    y = oracle.correlate(x, g)
+    assert np.max(np.abs(y - float(np.float32(c)) * g.sum())) < 1e-12
+    assert abs(g.sum() - 1.0) < 1e-6
+    w = rnd_w(3, 3)
+    y = oracle.correlate(x, w)
+    assert np.max(np.abs(y - float(np.float32(c)) * w.sum())) < 1e-12
+
+
+# ---------------------------------------------------------------------- linearity
+
+def test_linear_in_kernel():
+    x = rnd_vol(4, (7, 8, 9))
+    w1, w2 = rnd_w(5, 3), rnd_w(6, 3)
+    a, b = 0.37, -1.9
+    lhs = oracle.correlate(x, a * w1 + b * w2)
+    rhs = a * oracle.correlate(x, w1) + b * oracle.correlate(x, w2)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12
+
+
+def test_linear_in_input():
+    # small integers so that 3*x1 - 2*x2 is exact in float32
+    x1 = np.floor(rnd_vol(7, (6, 7, 8), 0, 50)).astype(np.float32)
+    x2 = np.floor(rnd_vol(8, (6, 7, 8), 0, 50)).astype(np.float32)
+    w = rnd_w(9, 5)
+    lhs = oracle.correlate((3 * x1 - 2 * x2).astype(np.float32), w)
+    rhs = 3 * oracle.correlate(x1, w) - 2 * oracle.correlate(x2, w)
+    assert np.max(np.abs(lhs - rhs)) < 1e-10
+
+
+# ---------------------------------------------------------------------- separable = 3 passes
+
+def _pass_1d(v, g, axis):
+    """1-D clamp-to-edge correlation along one axis, written independently of the oracle."""
+    r = (len(g) - 1) // 2
+    pad = [(0, 0)] * v.ndim
+    pad[axis] = (r, r)
+    vp = np.pad(v, pad, mode="edge")
+    out = np.zeros_like(v)
+    n = v.shape[axis]
+    for i, gi in enumerate(g):
+        sl = [slice(None)] * v.ndim
+        sl[axis] = slice(i, i + n)
+        out += float(gi) * vp[tuple(sl)]
+    return out
+
+
+@pytest.mark.parametrize("k,sigma", [(3, 1.0), (5, 1.5), (7, 7 / 3)])
+def test_separable_gaussian_equals_three_passes(k, sigma):
+    x = rnd_vol(10, (9, 6, 11), 0, 1)
+    g = oracle.gaussian_1d(k, sigma)
+    y = oracle.correlate(x, oracle.separable_weights(g, g, g))
+    t = x.astype(np.float64)
+    for axis in (2, 1, 0):      # x, then y, then z
+        t = _pass_1d(t, g, axis)
+    assert np.max(np.abs(y - t)) < 1e-12
+
+
+def test_separable_distinct_axes_orientation():
+    # different 1-D profiles per axis pin which weight index runs along which axis
+    x = rnd_vol(11, (5, 6, 7))
+    gx = np.array([0.1, 0.5, 0.2], np.float32)
+    gy = np.array([0.3, -0.4, 0.9], np.float32)
+    gz = np.array([-0.6, 0.25, 0.05], np.float32)
+    y = oracle.correlate(x, oracle.separable_weights(gx, gy, gz))
+    t = _pass_1d(_pass_1d(_pass_1d(x.astype(np.float64), gx, 2), gy, 1), gz, 0)
+    assert np.max(np.abs(y - t)) < 1e-12
+
+
+# ---------------------------------------------------------------------- library special cases
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_matches_scipy_nearest(k):
+    ndimage = pytest.importorskip("scipy.ndimage")
+    x = rnd_vol(12 + k, (6, 7, 5))
+    w = rnd_w(20 + k, k)
+    ref = ndimage.correlate(x.astype(np.float64), w, mode="nearest")
+    assert np.max(np.abs(oracle.correlate(x, w) - ref)) < 1e-12
+
+
+def test_matches_torch_replicate_conv3d():
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    x = rnd_vol(30, (5, 8, 6))
+    w = rnd_w(31, 3)
+    xt = torch.from_numpy(x.astype(np.float64))[None, None]
+    ref = F.conv3d(F.pad(xt, (1, 1, 1, 1, 1, 1), mode="replicate"),
+                   torch.from_numpy(w)[None, None])[0, 0].numpy()
+    assert np.max(np.abs(oracle.correlate(x, w) - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------------- hand-derived closed forms
+
+def test_hot_voxel_gives_flipped_footprint():
+    x = np.zeros((7, 7, 7), np.float32)
+    p = (3, 3, 3)          # (z, y, x)
+    x[p] = 1.0
+    w = rnd_w(40, 3)
+    y = oracle.correlate(x, w)
+    # y(i) = sum_d w[d] x(i+d-r) = w[p - i + r] for |p - i| <= r, else 0
+    for iz in range(7):
+        for iy in range(7):
+            for ix in range(7):
+                dz, dy, dx = p[0] - iz + 1, p[1] - iy + 1, p[2] - ix + 1
+                if 0 <= dz < 3 and 0 <= dy < 3 and 0 <= dx < 3:
+                    assert y[iz, iy, ix] == w[dz, dy, dx]
+                else:
+                    assert y[iz, iy, ix] == 0.0
+
+
+def test_ramp_interior_unchanged_faces_shifted():
+    z, yy, xx = np.meshgrid(np.arange(4), np.arange(4), np.arange(4), indexing="ij")
+    v = (xx + 4 * yy + 16 * z).astype(np.float32)
+    g = oracle.gaussian_1d(3, 1.0)
+    y = oracle.correlate(v, oracle.separable_weights(g, g, g))
+    # per axis the filter maps coordinate i to E[clamp(i + A)], A in {-1,0,1} with
+    # probabilities g: interior i -> i, i = 0 -> g[2] (only the +1 tap moves), i = 3 -> 3 - g[0]
+    g0, g2 = float(g[0]), float(g[2])
+    s = float(np.sum(g.astype(np.float64)))
+
+    def m(i):
+        if i == 0:
+            return (0 * (g0 + float(g[1])) + 1 * g2)
+        if i == 3:
+            return (2 * g0 + 3 * (float(g[1]) + g2))
+        return i * s
+    for iz in range(4):
+        for iy in range(4):
+            for ix in range(4):
+                expect = (m(ix) + 4 * m(iy) + 16 * m(iz)) * s * s
+                assert abs(y[iz, iy, ix] - expect) < 1e-12
+    assert abs(y[1, 2, 1] - (1 + 8 + 16)) < 1e-6           # interior: unchanged
+
+
+def _read_golden(name):
+    spec = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            spec[key] = vals
+    return spec
+
+
+def test_golden_fillrange_then_gaussian_blur():
+    spec = _read_golden("fillrange_teaser_64.txt")
+    nx, ny, nz = (int(v) for v in spec["dims"])
+    assert spec["format"] == ["uint8"]
+    lo, hi = (float(v) for v in spec["range"])
+    x0, y0, z0, x1, y1, z1 = (int(v) for v in spec["fillrange"])
+    fill = float(spec["fillvalue"][0])
+    code = int(round((fill - lo) / (hi - lo) * 255))
+    vol = np.zeros((nz, ny, nx), np.uint8)
+    vol[z0:z1, y0:y1, x0:x1] = code
+    kind, k, sigma = spec["filter"][0], int(spec["filter"][1]), float(spec["filter"][2])
+    assert kind == "gaussian" and k == 3
+    y = oracle.correlate(vol, oracle.gaussian_weights(k, sigma), lo, hi)
+    # closed form: exact sampled weights g = (e, 1, e)/(1 + 2e), e = exp(-1/(2 sigma^2));
+    # per axis the fraction of the kernel landing inside [first, last) is
+    #   0 at distance >= 2 outside, e/(1+2e) on the border voxel, 1 - e/(1+2e) on the
+    #   first/last filled voxel, 1 deeper inside.
+    e = math.exp(-1.0 / (2 * sigma * sigma))
+    g0 = e / (1 + 2 * e)
+
+    def frac(i, a, b):
+        if i < a - 1 or i > b:
+            return 0.0
+        if i == a - 1 or i == b:
+            return g0
+        if i == a or i == b - 1:
+            return 1.0 - g0
+        return 1.0
+
+    pts = [(0, 0, 0), (1, 1, 1), (2, 2, 2), (32, 32, 32), (0, 32, 32), (1, 32, 32),
+           (63, 63, 63), (62, 62, 62), (63, 1, 32), (61, 62, 0)]
+    for (ix, iy, iz) in pts:
+        expect = fill * frac(ix, x0, x1) * frac(iy, y0, y1) * frac(iz, z0, z1)
+        assert abs(y[iz, iy, ix] - expect) < 2e-7, (ix, iy, iz)
+
+
+# ---------------------------------------------------------------------- Gaussian construction
+
+@pytest.mark.parametrize("k,sigma", [(3, 1.0), (5, 1.5), (7, 7 / 3), (9, 3.0)])
+def test_gaussian_1d_properties(k, sigma):
+    g = oracle.gaussian_1d(k, sigma).astype(np.float64)
+    r = k // 2
+    assert abs(g.sum() - 1.0) < 1e-6
+    assert np.array_equal(g, g[::-1])
+    for d in range(1, r + 1):
+        assert abs(g[r + d] / g[r] - math.exp(-d * d / (2 * sigma * sigma))) < 1e-6
+
+
+# ---------------------------------------------------------------------- quantisation
+
+def test_quantize_ties_and_clamps():
+    v = np.array([2.5, 3.5, -1.0, 300.0, 127.2, 127.7, 0.0, 255.0]) / 255.0
+    t, q, tie = oracle.quantize(v, oracle.U8, 0.0, 1.0)
+    assert list(q) == [2, 4, 0, 255, 127, 128, 0, 255]
+    assert list(tie) == [True, True, False, False, False, False, False, False]
+    t, q, tie = oracle.quantize(np.array([0.5]), oracle.U16, 0.0, 1.0)
+    assert q[0] == round(0.5 * 65535)   # 32767.5 -> 32768 (even)
+    assert tie[0]
+
+
+# ---------------------------------------------------------------------- points == full
+
+def test_points_match_full_volume():
+    x = rnd_vol(50, (6, 5, 7))
+    w = rnd_w(51, 5)
+    full = oracle.correlate(x, w)
+    idx = np.arange(x.size)
+    pts = oracle.correlate_points(x, w, idx)
+    assert np.array_equal(pts, full.ravel())
+
+
+# ---------------------------------------------------------------------- gradients
+
+def test_adjoint_dot_product():
+    x = rnd_vol(60, (6, 7, 5))
+    yv = rnd_vol(61, (6, 7, 5)).astype(np.float64)
+    w = rnd_w(62, 5)
+    cx = oracle.correlate(x, w)
+    gx, gw = oracle.correlate_backward(x, yv, w)
+    assert abs(np.sum(cx * yv) - np.sum(x.astype(np.float64) * gx)) < 1e-10
+    # gw[d] = <C_{e_d} x, y>
+    for d in [0, 17, 62, 124]:
+        e = np.zeros(125)
+        e[d] = 1.0
+        assert abs(np.sum(oracle.correlate(x, e) * yv) - gw.ravel()[d]) < 1e-11
+
+
+def test_backward_input_points_match_scatter():
+    gy = rnd_vol(63, (4, 6, 5)).astype(np.float64)
+    x = rnd_vol(64, (4, 6, 5))
+    w = rnd_w(65, 5)             # k larger than one axis: several taps fold on a face
+    gx, _ = oracle.correlate_backward(x, gy, w, need_gw=False)
+    pts = oracle.backward_input_points(gy, w, np.arange(gy.size))
+    assert np.max(np.abs(pts - gx.ravel())) < 1e-12
+
+
+def test_gradients_match_central_differences():
+    x = rnd_vol(70, (5, 6, 7), 0, 1)
+    target = rnd_vol(71, (5, 6, 7), 0, 1).astype(np.float64)
+    w = rnd_w(72, 3) * 0.1
+    n = x.size
+
+    def loss(wv, xv):
+        return float(np.mean((oracle.correlate(xv, wv) - target) ** 2))
+
+    y = oracle.correlate(x, w)
+    gy = 2.0 * (y - target) / n
+    gx, gw = oracle.correlate_backward(x, gy, w)
+    h = 1e-3
+    for d in [0, 4, 13, 26]:
+        e = np.zeros(27)
+        e[d] = h
+        fd = (loss(w + e.reshape(3, 3, 3), x) - loss(w - e.reshape(3, 3, 3), x)) / (2 * h)
+        assert abs(fd - gw.ravel()[d]) < 1e-9
+    # input gradient on float32-exact perturbations (h a power of two)
+    hx = 2.0 ** -10
+    for j in [0, 37, n - 1]:
+        xp = x.copy().ravel()
+        xm = x.copy().ravel()
+        xp[j] += np.float32(hx)
+        xm[j] -= np.float32(hx)
+        fd = (loss(w, xp.reshape(x.shape)) - loss(w, xm.reshape(x.shape))) / (2 * hx)
+        assert abs(fd - gx.ravel()[j]) < 1e-9
+
+
+def test_gradients_match_torch_autograd():
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    x = rnd_vol(80, (6, 5, 7))
+    gy = rnd_vol(81, (6, 5, 7)).astype(np.float64)
+    w = rnd_w(82, 5)
+    xt = torch.from_numpy(x.astype(np.float64))[None, None].requires_grad_(True)
+    wt = torch.from_numpy(w)[None, None].requires_grad_(True)
+    y = F.conv3d(F.pad(xt, (2,) * 6, mode="replicate"), wt)
+    y.backward(torch.from_numpy(gy)[None, None])
+    gx, gw = oracle.correlate_backward(x, gy, w)
+    assert np.max(np.abs(gx - xt.grad[0, 0].numpy())) < 1e-11
+    assert np.max(np.abs(gw - wt.grad[0, 0].numpy())) < 1e-11
+
+
+# ---------------------------------------------------------------------- a planted mistake
+
+def test_planted_zero_padding_is_caught():
+    """The scipy pin distinguishes clamp-to-edge from zero padding (mode='constant')."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    x = rnd_vol(90, (5, 5, 5), 0.5, 1.0)
+    w = rnd_w(91, 3)
+    wrong = ndimage.correlate(x.astype(np.float64), w, mode="constant")
+    assert np.max(np.abs(oracle.correlate(x, w) - wrong)) > 1e-3

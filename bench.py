@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""ApplyFilter benchmark on one GB300 (or N replicas under torchrun).
+
+Workload (one step = the whole filter path over one volume): a 512^3 uint8 CT-like
+volume (32 Gaussian blobs + noise, mapping range [0,1]) filtered twice to float32:
+  1. a normalised 5^3 Gaussian, sigma 1.5 (built per step, separable path), and
+  2. the 7-point Laplacian as a dense 3^3 kernel (direct FP32 path).
+Gvoxel/s counts output voxels (2 x 512^3 per step).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MiB write) before every timed step, outside the
+step's own CUDA events.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (512, 512, 512)
+SEED = 220310213 + 1
+METRIC = "ApplyFilter Gvoxel/s & % roofline, split-TC vs plain FP32 at <=1e-5 err, 1 GB300"
+WORKLOAD = "ct512_u8_to_f32: gaussian5 sigma1.5 (separable) + laplacian3 (dense direct)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.split(",") for ln in self.file.read().splitlines() if ln.count(",") >= 8]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+def workload_host():
+    import synth
+    return synth.volume("blobs", synth.U8, DIMS, SEED)
+
+
+def oracle_sample_rate(vol, seconds: float, seed: int = 7):
+    """Times the FP64 oracle on random voxels of the workload; returns voxels/s (both
+    filters, each output counted once) and the sample description."""
+    import oracle
+    w_g = oracle.gaussian_weights(5, float(np.float32(1.5)))
+    w_l = oracle.laplacian_3()
+    rng = np.random.default_rng(seed)
+    n = 4096
+    while True:
+        idx = rng.integers(0, vol.size, n)
+        t0 = time.perf_counter()
+        oracle.correlate_points(vol, w_g, idx, 0.0, 1.0)
+        oracle.correlate_points(vol, w_l, idx, 0.0, 1.0)
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= 1 << 26:
+            break
+        n = int(min(n * max(2.0, seconds / max(dt, 1e-3)), 1 << 26))
+    return 2 * n / dt, n, dt
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import oracle
+    import paper_2203_10213_gb300 as vkt
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    vol = workload_host()
+    src = torch.from_numpy(vol).to(dev)
+    out_g = torch.empty(vol.shape, dtype=torch.float32, device=dev)
+    out_l = torch.empty(vol.shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    v_src = vkt.StructuredVolume.from_tensor(src, 0.0, 1.0)
+    v_g = vkt.StructuredVolume.from_tensor(out_g, 0.0, 1.0)
+    v_l = vkt.StructuredVolume.from_tensor(out_l, 0.0, 1.0)
+    lap = vkt.Filter.dense(oracle.laplacian_3().astype(np.float32))
+    lib = vkt._lib
+    vkt.set_policy(stream=stream)
+
+    def step(evs=None):
+        g = vkt.Filter.gaussian(5, 1.5)          # filter construction is part of the path
+        if evs:
+            evs[0].record(stream)
+        vkt.check(lib.vktApplyFilterSV(v_g.handle, v_src.handle, g.handle))
+        if evs:
+            evs[1].record(stream)
+        vkt.check(lib.vktApplyFilterSV(v_l.handle, v_src.handle, lap.handle))
+        if evs:
+            evs[2].record(stream)
+        g.destroy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    vkt.synchronize()
+
+    K = args.steps
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+    kern_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    launches0 = vkt.launch_count()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()                             # L2 flush, outside the step's events
+        step_ev[i][0].record(stream)
+        step(kern_ev[i])
+        step_ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = vkt.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    vkt.synchronize()
+
+    step_ms = [a.elapsed_time(b) for a, b in step_ev]
+    sep_ms = [e[0].elapsed_time(e[1]) for e in kern_ev]
+    dir_ms = [e[1].elapsed_time(e[2]) for e in kern_ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    vox = float(np.prod(DIMS))
+    value = 2 * vox * world / (ms_per_step * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if rank == 0 or world > 1:
+        host_in = torch.from_numpy(vol).pin_memory()
+        host_g = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+        host_l = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+        E = max(1, args.e2e_steps)
+
+        def e2e_step():
+            vkt.check(lib.vktStructuredVolumeSetData(v_src.handle, host_in.data_ptr()))
+            step()
+            vkt.check(lib.vktStructuredVolumeCopyToHost(v_g.handle, host_g.data_ptr()))
+            vkt.check(lib.vktStructuredVolumeCopyToHost(v_l.handle, host_l.data_ptr()))
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(E):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        vkt.synchronize()
+        e2e_ms = a.elapsed_time(b) / E
+        et = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e_ms = float(et.item())
+        e2e = {"value": round(2 * vox * world / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gvoxel/s",
+               "h2d_bytes_per_step": int(host_in.numel()),
+               "d2h_bytes_per_step": int(host_g.numel() * 4 + host_l.numel() * 4),
+               "ms_per_step": round(e2e_ms, 4)}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    alg_bytes = vox * (1 + 4)                   # u8 in, f32 out per launch
+    kernels = []
+    for name, ms in (("separable gaussian5", sep_ms), ("direct laplacian3", dir_ms)):
+        avg = statistics.mean(ms)
+        gbs = alg_bytes / (avg * 1e-3) / 1e9
+        kernels.append({"kernel": name, "avg_ms": round(avg, 5), "achieved_gbs": round(gbs, 1),
+                        "frac_hbm": round(gbs / hbm, 4),
+                        "gvoxel_s": round(vox / (avg * 1e-3) / 1e9, 2)})
+    dom = max(kernels, key=lambda k: k["avg_ms"])
+    roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"],
+                "peak": hbm, "unit": "GB/s", "frac": dom["frac_hbm"],
+                "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
+                "algorithmic_bytes_per_launch": int(alg_bytes), "traffic": None}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        rate, n, dt = oracle_sample_rate(vol, args.cpu_seconds)
+        cpu = {"value": round(rate / 1e9, 6), "unit": "Gvoxel/s", "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"{n} random voxels of the 512^3 volume, both filters, FP64 C, {dt:.1f} s"}
+
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded CT-like blobs, no dataset)",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "src": "u8 range [0,1]",
+                       "dst": "f32", "filters": ["gaussian k5 sigma1.5 separable",
+                                                 "laplacian 7-point as dense k3"],
+                       "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk,
+            "wall_s_timed_loop": round(wall, 3)}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (oracle)
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    vol = workload_host()
+    total = max(1, args.steps + args.warmup)
+    per_step = max(0.01, 60.0 / total)
+    rate, n, dt = oracle_sample_rate(vol, per_step)
+    rng = np.random.default_rng(11)
+    w_g = oracle.gaussian_weights(5, float(np.float32(1.5)))
+    w_l = oracle.laplacian_3()
+    times = []
+    for i in range(total):
+        idx = rng.integers(0, vol.size, n)
+        t0 = time.perf_counter()
+        oracle.correlate_points(vol, w_g, idx, 0.0, 1.0)
+        oracle.correlate_points(vol, w_l, idx, 0.0, 1.0)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    value = 2 * n / sec / 1e9
+    cpu = {"value": round(value, 6), "unit": "Gvoxel/s", "cores": oracle.num_threads(),
+           "kind": "oracle", "sample": f"{n} random voxels per step of the 512^3 volume, both filters"}
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Gvoxel/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(sec * 1e3, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded CT-like blobs)",
+            "config": {"workload": WORKLOAD, "dims": list(DIMS), "src": "u8 range [0,1]",
+                       "dst": "f32 (oracle computes f64)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(value, 6), "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

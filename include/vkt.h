@@ -1,0 +1,239 @@
+/*
+ * vkt.h -- C ABI of the GB300 ApplyFilter library.
+ *
+ * The calls follow the style of the paper's C99 interface (Sec. 3.3 and the ANSI C99
+ * listing of Fig. exampleCvsCPP): opaque handles, the out-handle as first argument, a
+ * "SV" suffix for the structured-volume variant of an algorithm, and a volume created
+ * from its dims, data format, cell size and value range.  The paper prints only the
+ * volume calls; the filter calls are this library's own, written in the same style.
+ *
+ * Conventions that hold for every call:
+ *   - Every call returns a vktError and never throws or aborts.
+ *   - All device memory is on the CUDA device that is current on the calling thread.
+ *     Pointers named devPtr are device pointers; pointers named host* are host
+ *     pointers (pinned memory makes the asynchronous copies truly asynchronous).
+ *   - Work is enqueued on the stream of the calling thread's execution policy
+ *     (vktSetThreadExecutionPolicy; the default is the legacy default stream) and the
+ *     call returns without waiting.  Launch errors are returned at once; a device-side
+ *     timeout of a bounded wait is recorded on the device and returned by the next
+ *     vktSynchronize.
+ *   - Handles are owned by the caller and released with the matching Destroy call.
+ *     Destroy does not wait for work in flight: synchronise first.
+ *   - Voxels are stored x fastest, then y, then z, with no row padding.
+ */
+#ifndef VKT_H
+#define VKT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Entry points keep default visibility when the library hides everything else. */
+#if defined(__GNUC__)
+#define VKT_API __attribute__((visibility("default")))
+#else
+#define VKT_API
+#endif
+
+typedef enum vktError {
+    VKT_NO_ERROR = 0,
+    VKT_ERROR_INVALID_VALUE = 1,    /* bad size, format, range, NULL pointer, aliasing */
+    VKT_ERROR_INVALID_HANDLE = 2,   /* NULL or already destroyed handle */
+    VKT_ERROR_DIMS_MISMATCH = 3,    /* dst and src dims differ */
+    VKT_ERROR_UNSUPPORTED = 4,      /* even or too large kernel, path not available */
+    VKT_ERROR_OUT_OF_MEMORY = 5,
+    VKT_ERROR_NO_DEVICE = 6,        /* no CUDA device or driver */
+    VKT_ERROR_CUDA = 7,             /* any other CUDA runtime or driver error */
+    VKT_ERROR_DEVICE_TIMEOUT = 8    /* a bounded device wait gave up (see vktSynchronize) */
+} vktError;
+
+/* Voxel storage formats (Fig. exampleCvsCPP: vktDataFormatUint8). */
+typedef enum vktDataFormat {
+    vktDataFormatUint8 = 0,
+    vktDataFormatUint16 = 1,
+    vktDataFormatFloat32 = 2
+} vktDataFormat;
+
+/* Filter evaluation paths; VKT_PATH_AUTO picks one per call from the filter and sizes. */
+typedef enum vktFilterPath {
+    VKT_PATH_AUTO = 0,
+    VKT_PATH_DIRECT = 1,       /* FP32 CUDA-core tap loop over all k^3 taps */
+    VKT_PATH_SEPARABLE = 2,    /* three fused 1-D passes; separable filters only */
+    VKT_PATH_TENSOR = 3        /* FP16 hi/lo split on tcgen05 tensor cores, float32 data */
+} vktFilterPath;
+
+typedef struct vktStructuredVolume_impl* vktStructuredVolume;
+typedef struct vktFilter_impl* vktFilter;
+
+/*
+ * Thread-local execution policy (Sec. 3.1: the thread-local ExecutionPolicy set and read
+ * with SetThreadExecutionPolicy / GetThreadExecutionPolicy, which also switches debug
+ * messages and the printing of algorithm times).  There is no device field: every call
+ * runs on the current CUDA device.
+ *   stream      cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   printTimes  nonzero: time each call with CUDA events and print it to stderr
+ *               (this synchronises the stream after the call)
+ *   debug       nonzero: print path choices and launch shapes to stderr
+ *   path        a vktFilterPath forcing the evaluation path (VKT_PATH_AUTO = choose)
+ */
+typedef struct vktExecutionPolicy {
+    void* stream;
+    int32_t printTimes;
+    int32_t debug;
+    int32_t path;
+} vktExecutionPolicy;
+
+VKT_API vktError vktSetThreadExecutionPolicy(vktExecutionPolicy policy);
+VKT_API vktError vktGetThreadExecutionPolicy(vktExecutionPolicy* policy);
+
+/* Short English description of an error code; never NULL. */
+VKT_API const char* vktGetErrorString(vktError error);
+
+/*
+ * Waits for the policy stream and reports device-side failures recorded since the last
+ * call: VKT_ERROR_DEVICE_TIMEOUT if a bounded wait inside a kernel gave up (the kernel
+ * then skipped its work and its output is undefined), VKT_ERROR_CUDA on an asynchronous
+ * CUDA error.  Clears the recorded device status.
+ */
+VKT_API vktError vktSynchronize(void);
+
+/* Number of kernels this library has launched in this process (all threads). */
+VKT_API vktError vktGetLaunchCount(uint64_t* count);
+
+/* ------------------------------------------------------------------ structured volumes */
+
+/*
+ * Creates a structured volume (Sec. 3.2 "Volume Types"; argument order of the C99
+ * listing in Fig. exampleCvsCPP: dims, format, cell size, range) owning
+ * dx*dy*dz voxels of device memory on the current device, zero filled.
+ *   dx,dy,dz  >= 1 voxels per axis
+ *   format    storage format of one voxel
+ *   sx,sy,sz  cell size (metadata, > 0)
+ *   lo,hi     value range: an integer code q maps to lo + (hi-lo)*q/(2^N-1); for
+ *             float32 voxels the stored value is the value and the range is metadata.
+ *             Integer formats need hi != lo.
+ * Errors: INVALID_VALUE (NULL out, bad dims/format/range), OUT_OF_MEMORY, NO_DEVICE.
+ */
+VKT_API vktError vktStructuredVolumeCreate(vktStructuredVolume* volume, int32_t dx, int32_t dy,
+                                   int32_t dz, vktDataFormat format, float sx, float sy,
+                                   float sz, float lo, float hi);
+
+/*
+ * Creates a non-owning view of dx*dy*dz voxels at devPtr (for instance the storage of
+ * a torch tensor).  devPtr must be aligned to the voxel size and stay valid while the
+ * view is used; Destroy never frees it.  Same arguments and errors as Create, plus
+ * INVALID_VALUE for a NULL or misaligned devPtr.
+ */
+VKT_API vktError vktStructuredVolumeCreateView(vktStructuredVolume* volume, void* devPtr,
+                                       int32_t dx, int32_t dy, int32_t dz,
+                                       vktDataFormat format, float sx, float sy, float sz,
+                                       float lo, float hi);
+
+/* Releases the handle (and the device memory of an owning volume). */
+VKT_API vktError vktStructuredVolumeDestroy(vktStructuredVolume volume);
+
+VKT_API vktError vktStructuredVolumeGetDims(vktStructuredVolume volume, int32_t* dx, int32_t* dy,
+                                    int32_t* dz);
+VKT_API vktError vktStructuredVolumeGetDataFormat(vktStructuredVolume volume, vktDataFormat* format);
+VKT_API vktError vktStructuredVolumeGetCellSize(vktStructuredVolume volume, float* sx, float* sy,
+                                        float* sz);
+VKT_API vktError vktStructuredVolumeGetVoxelMapping(vktStructuredVolume volume, float* lo, float* hi);
+VKT_API vktError vktStructuredVolumeSetVoxelMapping(vktStructuredVolume volume, float lo, float hi);
+/* Device pointer of the voxels and their size in bytes. */
+VKT_API vktError vktStructuredVolumeGetData(vktStructuredVolume volume, void** devPtr);
+VKT_API vktError vktStructuredVolumeGetSizeInBytes(vktStructuredVolume volume, uint64_t* bytes);
+
+/* Asynchronous copies of all voxels between host memory and the volume (policy stream). */
+VKT_API vktError vktStructuredVolumeSetData(vktStructuredVolume volume, const void* hostPtr);
+VKT_API vktError vktStructuredVolumeCopyToHost(vktStructuredVolume volume, void* hostPtr);
+
+/* ------------------------------------------------------------------ filters */
+
+/* Largest supported kernel size. */
+#define VKT_MAX_FILTER_SIZE 9
+
+/*
+ * Creates a dense k*k*k filter ("user-specified convolution kernel", Sec. 3.2 "Volume
+ * Manipulation").  k odd, 1 <= k <= VKT_MAX_FILTER_SIZE.  hostWeights holds k^3 floats,
+ * index (c*k + b)*k + a for the offsets (a-r, b-r, c-r) along (x, y, z), r = (k-1)/2;
+ * NULL gives all zeros.  The filter value at voxel (x,y,z) is the clamp-to-edge
+ * correlation sum_{a,b,c} w[c][b][a] * v(x+a-r, y+b-r, z+c-r).
+ * Errors: INVALID_VALUE (NULL out), UNSUPPORTED (even or too large k), OUT_OF_MEMORY.
+ */
+VKT_API vktError vktFilterCreate(vktFilter* filter, int32_t k, const float* hostWeights);
+
+/* Rank-1 filter w[c][b][a] = wz[c] * wy[b] * wx[a] from three k-vectors (host memory). */
+VKT_API vktError vktFilterCreateSeparable(vktFilter* filter, int32_t k, const float* wx,
+                                  const float* wy, const float* wz);
+
+/*
+ * Gaussian blur filter (the filter of the teaser figure and of Sec. 4.3): the sampled
+ * Gaussian exp(-d^2 / (2 sigma^2)) at the integer offsets d in [-r, r], divided by its
+ * sum in FP64 and stored as float32, used as the three vectors of a separable filter.
+ * sigma > 0.
+ */
+VKT_API vktError vktFilterCreateGaussian(vktFilter* filter, int32_t k, float sigma);
+
+/* Replaces the weights by k^3 dense weights (the filter stops being separable). */
+VKT_API vktError vktFilterSetWeights(vktFilter filter, const float* hostWeights);
+
+/*
+ * Divides the weights by their sum, computed in FP64 (for a separable filter each
+ * vector is divided by its own sum).  INVALID_VALUE if the sum is zero or not finite.
+ */
+VKT_API vktError vktFilterNormalize(vktFilter filter);
+
+VKT_API vktError vktFilterGetSize(vktFilter filter, int32_t* k);
+/* 1 if the filter is stored as three vectors, else 0. */
+VKT_API vktError vktFilterIsSeparable(vktFilter filter, int32_t* separable);
+/* Dense k^3 float32 weights (for a separable filter: the float32-rounded products). */
+VKT_API vktError vktFilterGetWeights(vktFilter filter, float* hostWeights);
+/* The three vectors of a separable filter (UNSUPPORTED for a dense one). */
+VKT_API vktError vktFilterGetSeparableWeights(vktFilter filter, float* wx, float* wy, float* wz);
+VKT_API vktError vktFilterDestroy(vktFilter filter);
+
+/* ------------------------------------------------------------------ ApplyFilter */
+
+/*
+ * ApplyFilter (Sec. 3.2 "Volume Manipulation"): dst = the filter applied to src, every
+ * voxel, clamp-to-edge at the faces.  Source codes are mapped through the source range
+ * first; the float result is written to dst directly (float32 dst) or quantised
+ * through the dst range, q = clamp(round-half-even((v-lo)/(hi-lo)*(2^N-1)), 0, 2^N-1).
+ * dst and src must have equal dims (else DIMS_MISMATCH) and must not overlap in memory
+ * (else INVALID_VALUE); their formats may differ.  UNSUPPORTED when the policy forces a
+ * path that cannot evaluate this filter (separable path with a dense filter, tensor
+ * path with a non-float32 volume or k < 3).
+ */
+VKT_API vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter);
+
+/*
+ * Batched ApplyFilter over n independent (dst[i], src[i], filters[i]) triples, with
+ * the rules of vktApplyFilterSV for each triple, in one persistent launch over a
+ * work list of bricks.  The launch is captured in a CUDA graph that is reused while
+ * the same handles are passed again.  n >= 1.
+ */
+VKT_API vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
+                               vktFilter* filters);
+
+/*
+ * Gradients of y = ApplyFilter(src, filter) for float32 volumes, given gradDst = dL/dy:
+ *   gradSrc     (float32 volume, dims of src, may be NULL) receives dL/dsrc, the exact
+ *               adjoint of the clamp-to-edge correlation (taps that fall outside a face
+ *               fold onto the face voxel);
+ *   gradWeights (device float*, k^3, may be NULL) receives dL/dw[c][b][a] =
+ *               sum_i gradDst[i] * src[clamp(i + (a-r, b-r, c-r))], reduced in FP64.
+ * src, gradDst and gradSrc must be float32 with equal dims; gradSrc must not overlap
+ * gradDst or src.
+ */
+VKT_API vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeights,
+                                  vktStructuredVolume gradDst, vktStructuredVolume src,
+                                  vktFilter filter);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VKT_H */

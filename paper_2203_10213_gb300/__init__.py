@@ -1,0 +1,339 @@
+"""GB300 ApplyFilter: Python binding of the C ABI in include/vkt.h.
+
+This module only marshals arguments: every step of the filter runs in the CUDA kernels of
+libvkt.so.  PyTorch supplies device memory and streams.  Importing it loads (and if
+needed builds) the library and raises if that fails; there is no CPU fallback.
+
+Volumes are (nz, ny, nx) tensors, x fastest, of dtype uint8, uint16 or float32.
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes
+
+import numpy as np
+
+from . import _build
+from ._lib import ExecutionPolicy, load
+
+U8, U16, F32 = 0, 1, 2
+PATH_AUTO, PATH_DIRECT, PATH_SEPARABLE, PATH_TENSOR = 0, 1, 2, 3
+PATHS = {"auto": PATH_AUTO, "direct": PATH_DIRECT, "separable": PATH_SEPARABLE,
+         "tensor": PATH_TENSOR}
+MAX_FILTER_SIZE = 9
+
+ERRORS = {0: "VKT_NO_ERROR", 1: "VKT_ERROR_INVALID_VALUE", 2: "VKT_ERROR_INVALID_HANDLE",
+          3: "VKT_ERROR_DIMS_MISMATCH", 4: "VKT_ERROR_UNSUPPORTED",
+          5: "VKT_ERROR_OUT_OF_MEMORY", 6: "VKT_ERROR_NO_DEVICE", 7: "VKT_ERROR_CUDA",
+          8: "VKT_ERROR_DEVICE_TIMEOUT"}
+
+_lib = load()
+
+
+class VktError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib.vktGetErrorString(code).decode()
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}" + (f" ({what})" if what else ""))
+
+
+def check(code: int, what: str = "") -> None:
+    if code != 0:
+        raise VktError(code, what)
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _fmt_of_dtype(dtype) -> int:
+    torch = _torch()
+    table = {torch.uint8: U8, torch.float32: F32}
+    if hasattr(torch, "uint16"):
+        table[torch.uint16] = U16
+    if dtype not in table:
+        raise TypeError(f"unsupported voxel dtype {dtype}")
+    return table[dtype]
+
+
+def torch_dtype(fmt: int):
+    torch = _torch()
+    return {U8: torch.uint8, U16: torch.uint16, F32: torch.float32}[fmt]
+
+
+# ------------------------------------------------------------------ execution policy
+
+def get_policy() -> ExecutionPolicy:
+    pol = ExecutionPolicy()
+    check(_lib.vktGetThreadExecutionPolicy(ctypes.byref(pol)))
+    return pol
+
+
+def set_policy(stream=None, path="auto", debug=False, print_times=False) -> None:
+    pol = ExecutionPolicy()
+    pol.stream = ctypes.c_void_p(_stream_handle(stream))
+    pol.path = PATHS[path] if isinstance(path, str) else int(path)
+    pol.debug = int(bool(debug))
+    pol.printTimes = int(bool(print_times))
+    check(_lib.vktSetThreadExecutionPolicy(pol))
+
+
+@contextlib.contextmanager
+def policy(stream=None, path="auto", debug=False, print_times=False):
+    """Temporarily sets the calling thread's execution policy."""
+    old = get_policy()
+    set_policy(stream, path, debug, print_times)
+    try:
+        yield
+    finally:
+        check(_lib.vktSetThreadExecutionPolicy(old))
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        torch = _torch()
+        return int(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def synchronize() -> None:
+    """Waits for the policy stream; raises on a device-side timeout or CUDA error."""
+    check(_lib.vktSynchronize(), "vktSynchronize")
+
+
+def launch_count() -> int:
+    n = ctypes.c_uint64()
+    check(_lib.vktGetLaunchCount(ctypes.byref(n)))
+    return int(n.value)
+
+
+# ------------------------------------------------------------------ volumes
+
+class StructuredVolume:
+    """A structured volume handle (owning, or a view of a torch tensor)."""
+
+    def __init__(self, handle: ctypes.c_void_p, tensor=None):
+        self._h = handle
+        self.tensor = tensor          # keeps a viewed tensor alive
+
+    @classmethod
+    def create(cls, dims, fmt: int, cell=(1.0, 1.0, 1.0), lo: float = 0.0, hi: float = 1.0):
+        h = ctypes.c_void_p()
+        nx, ny, nz = dims
+        check(_lib.vktStructuredVolumeCreate(ctypes.byref(h), nx, ny, nz, fmt, *cell, lo, hi),
+              "vktStructuredVolumeCreate")
+        return cls(h)
+
+    @classmethod
+    def from_tensor(cls, t, lo: float = 0.0, hi: float = 1.0, cell=(1.0, 1.0, 1.0)):
+        if t.dim() != 3 or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError("volume tensors are contiguous CUDA tensors of shape (nz, ny, nx)")
+        nz, ny, nx = t.shape
+        h = ctypes.c_void_p()
+        check(_lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(t.data_ptr()),
+                                                 nx, ny, nz, _fmt_of_dtype(t.dtype), *cell, lo,
+                                                 hi), "vktStructuredVolumeCreateView")
+        return cls(h, t)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def dims(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(_lib.vktStructuredVolumeGetDims(self._h, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c)))
+        return (a.value, b.value, c.value)
+
+    @property
+    def format(self) -> int:
+        f = ctypes.c_int()
+        check(_lib.vktStructuredVolumeGetDataFormat(self._h, ctypes.byref(f)))
+        return f.value
+
+    @property
+    def cell_size(self):
+        a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+        check(_lib.vktStructuredVolumeGetCellSize(self._h, ctypes.byref(a), ctypes.byref(b),
+                                                  ctypes.byref(c)))
+        return (a.value, b.value, c.value)
+
+    @property
+    def mapping(self):
+        lo, hi = ctypes.c_float(), ctypes.c_float()
+        check(_lib.vktStructuredVolumeGetVoxelMapping(self._h, ctypes.byref(lo), ctypes.byref(hi)))
+        return (lo.value, hi.value)
+
+    def set_mapping(self, lo: float, hi: float) -> None:
+        check(_lib.vktStructuredVolumeSetVoxelMapping(self._h, lo, hi))
+
+    @property
+    def data_ptr(self) -> int:
+        d = ctypes.c_void_p()
+        check(_lib.vktStructuredVolumeGetData(self._h, ctypes.byref(d)))
+        return int(d.value or 0)
+
+    @property
+    def nbytes(self) -> int:
+        n = ctypes.c_uint64()
+        check(_lib.vktStructuredVolumeGetSizeInBytes(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def set_data(self, host: np.ndarray) -> None:
+        """Asynchronous host-to-device copy of all voxels (keep `host` alive until synced)."""
+        host = np.ascontiguousarray(host)
+        if host.nbytes != self.nbytes:
+            raise ValueError("host array size does not match the volume")
+        check(_lib.vktStructuredVolumeSetData(self._h, ctypes.c_void_p(host.ctypes.data)))
+
+    def copy_to_host(self, out: np.ndarray) -> None:
+        if not out.flags["C_CONTIGUOUS"] or out.nbytes != self.nbytes:
+            raise ValueError("output array must be contiguous and match the volume size")
+        check(_lib.vktStructuredVolumeCopyToHost(self._h, ctypes.c_void_p(out.ctypes.data)))
+
+    def destroy(self) -> None:
+        if self._h is not None and self._h.value:
+            check(_lib.vktStructuredVolumeDestroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ filters
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Filter:
+    """A k x k x k filter (dense, separable or Gaussian)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def dense(cls, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        k = round(w.size ** (1 / 3))
+        if k ** 3 != w.size:
+            raise ValueError("dense weights hold k^3 values")
+        h = ctypes.c_void_p()
+        check(_lib.vktFilterCreate(ctypes.byref(h), k, _fptr(w)), "vktFilterCreate")
+        return cls(h)
+
+    @classmethod
+    def separable(cls, gx, gy, gz):
+        gx, gy, gz = (np.ascontiguousarray(g, dtype=np.float32) for g in (gx, gy, gz))
+        h = ctypes.c_void_p()
+        check(_lib.vktFilterCreateSeparable(ctypes.byref(h), gx.size, _fptr(gx), _fptr(gy),
+                                            _fptr(gz)), "vktFilterCreateSeparable")
+        return cls(h)
+
+    @classmethod
+    def gaussian(cls, k: int, sigma: float):
+        h = ctypes.c_void_p()
+        check(_lib.vktFilterCreateGaussian(ctypes.byref(h), k, sigma), "vktFilterCreateGaussian")
+        return cls(h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def k(self) -> int:
+        k = ctypes.c_int32()
+        check(_lib.vktFilterGetSize(self._h, ctypes.byref(k)))
+        return k.value
+
+    @property
+    def is_separable(self) -> bool:
+        s = ctypes.c_int32()
+        check(_lib.vktFilterIsSeparable(self._h, ctypes.byref(s)))
+        return bool(s.value)
+
+    def weights(self) -> np.ndarray:
+        k = self.k
+        w = np.empty((k, k, k), np.float32)
+        check(_lib.vktFilterGetWeights(self._h, _fptr(w)))
+        return w
+
+    def separable_weights(self):
+        k = self.k
+        g = [np.empty(k, np.float32) for _ in range(3)]
+        check(_lib.vktFilterGetSeparableWeights(self._h, *(_fptr(x) for x in g)))
+        return tuple(g)
+
+    def set_weights(self, w) -> None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.size != self.k ** 3:
+            raise ValueError("dense weights hold k^3 values")
+        check(_lib.vktFilterSetWeights(self._h, _fptr(w)))
+
+    def normalize(self) -> None:
+        check(_lib.vktFilterNormalize(self._h), "vktFilterNormalize")
+
+    def destroy(self) -> None:
+        if self._h is not None and self._h.value:
+            check(_lib.vktFilterDestroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ ApplyFilter
+
+def apply_filter(dst: StructuredVolume, src: StructuredVolume, filt: Filter, path="auto",
+                 stream=None) -> None:
+    """Enqueues dst = filter(src) on `stream` (default: torch's current stream)."""
+    with policy(stream=stream, path=path):
+        check(_lib.vktApplyFilterSV(dst.handle, src.handle, filt.handle), "vktApplyFilterSV")
+
+
+def apply_filter_batch(dsts, srcs, filters, stream=None) -> None:
+    n = len(dsts)
+    if not (len(srcs) == n == len(filters)):
+        raise ValueError("dsts, srcs and filters must have the same length")
+    arr = ctypes.c_void_p * n
+    d = arr(*(v.handle.value for v in dsts))
+    s = arr(*(v.handle.value for v in srcs))
+    f = arr(*(x.handle.value for x in filters))
+    with policy(stream=stream):
+        check(_lib.vktApplyFilterBatchSV(n, d, s, f), "vktApplyFilterBatchSV")
+
+
+def apply_filter_backward(grad_src, grad_weights, grad_dst: StructuredVolume,
+                          src: StructuredVolume, filt: Filter, stream=None) -> None:
+    """grad_src: StructuredVolume or None; grad_weights: float32 CUDA tensor (k^3) or None."""
+    gs = grad_src.handle if grad_src is not None else None
+    gw = ctypes.c_void_p(grad_weights.data_ptr()) if grad_weights is not None else None
+    with policy(stream=stream):
+        check(_lib.vktApplyFilterBackwardSV(gs, gw, grad_dst.handle, src.handle, filt.handle),
+              "vktApplyFilterBackwardSV")
+
+
+def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
+                  dst_range=(0.0, 1.0), path="auto", out=None):
+    """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty(src_t.shape, dtype=dst_dtype or torch.float32, device=src_t.device)
+    src = StructuredVolume.from_tensor(src_t, *src_range)
+    dst = StructuredVolume.from_tensor(out, *dst_range)
+    apply_filter(dst, src, filt, path=path)
+    return out

@@ -1,0 +1,284 @@
+// vkt_direct.cu -- direct FP32 evaluation of ApplyFilter (Sec. 3.2, "Volume Manipulation":
+// a user-specified convolution kernel applied to every cell), all k^3 taps on CUDA cores.
+//
+// Each CTA owns a TX x TY column of output voxels and marches through a chunk of z.  Input
+// planes (with an r-voxel halo) arrive by TMA into a ring of raw tiles, are converted to
+// float with clamp-to-edge into a float tile, and every input plane is multiplied into the
+// K output planes it touches; each thread keeps K x RY x RX accumulators in registers, so
+// an input plane is read from shared memory once per thread window and never again.
+//   K <= 3 : the K accumulator planes rotate by unrolling the plane loop K times;
+//   K >= 5 : they rotate by shifting once per plane (less code for the same arithmetic).
+// Weights travel as kernel parameters and enter the FMAs as constant-bank operands.
+#include <algorithm>
+#include <cstdio>
+
+#include "vkt_internal.h"
+#include "vkt_tile.cuh"
+
+namespace vkt {
+namespace {
+
+constexpr int NT = 256;          // threads per CTA, 16 x 16
+constexpr int BX = 16, BY = 16;
+constexpr int STAGES = 4;        // raw tiles in flight per CTA
+
+template <int K>
+struct DenseW {
+    float w[K * K * K];
+};
+
+struct DirectArgs {
+    const void* src;
+    void* dst;
+    int nx, ny, nz;
+    int sfmt, dfmt;
+    int zchunk;
+    int use_tma;
+    float a0, a1, qmax;
+    unsigned* status;
+};
+
+template <int K>
+struct DirectCfg {
+    static constexpr int RX = (K == 9) ? 2 : 4;
+    static constexpr int RY = 2;
+    static constexpr bool ROT = K >= 5;
+    static constexpr int TX = BX * RX, TY = BY * RY;
+    using Geo = Brick<K, TX, TY>;
+};
+
+template <int K>
+__host__ __device__ constexpr size_t direct_smem_bytes(int sfmt)
+{
+    using Geo = typename DirectCfg<K>::Geo;
+    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+           2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
+}
+
+template <int K>
+__global__ void __launch_bounds__(NT)
+    k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
+{
+    using Cfg = DirectCfg<K>;
+    using Geo = typename Cfg::Geo;
+    constexpr int R = Geo::R, RX = Cfg::RX, RY = Cfg::RY;
+    constexpr int FH = Geo::FH, FP = Geo::FP;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    const int rawb = Geo::raw_bytes(p.sfmt);
+    const uint32_t txb = Geo::raw_tx(p.sfmt);
+    unsigned char* raw = smem + 128;
+    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int x0 = blockIdx.x * Cfg::TX, y0 = blockIdx.y * Cfg::TY;
+    const int zc0 = blockIdx.z * p.zchunk;
+    const int zc1 = min(zc0 + p.zchunk, p.nz);
+    if (zc0 >= zc1) return;
+    const int pfirst = zc0 - R;
+    const int nplanes = zc1 - zc0 + 2 * R;
+    const int xa = fmt_xalign(p.sfmt);
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        if (p.use_tma) prefetch_tensor_map(&tmap);
+    }
+    __syncthreads();
+    int issued = 0;   // TMA loads issued so far (thread 0 only)
+    if (p.use_tma && tid == 0) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(pfirst + s, 0, p.nz - 1));
+        }
+    }
+
+    ConvPlan<Geo, NT> plan;
+    plan.init(p.sfmt, p.nx, p.ny, x0, y0, tid);
+
+    float acc[K][RY][RX];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int i = 0; i < RY; ++i)
+#pragma unroll
+            for (int x = 0; x < RX; ++x) acc[s][i][x] = 0.f;
+
+    const int ox = x0 + tx * RX;
+    const int nvalid = p.nx - ox;
+    bool failed = false;
+
+    // One input plane: fetch, convert, multiply into the K output planes, retire one.
+    auto plane = [&](const int it, const int u) {
+        const int s = it % STAGES;
+        const unsigned char* rs = raw + s * rawb;
+        float* Fb = F + (it & 1) * FH * FP;
+        bool ok = true;
+        if (p.use_tma) {
+            ok = mbar_wait(&bars[s], (it / STAGES) & 1);
+        } else {
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), p.src, p.sfmt, p.nx, p.ny,
+                                    x0, y0, clampi(pfirst + it, 0, p.nz - 1), tid);
+            __syncthreads();
+        }
+        if (ok) plan.convert(rs, p.sfmt, Fb, tid);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            return;
+        }
+        if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(pfirst + it + STAGES, 0, p.nz - 1));
+            ++issued;
+        }
+        // multiply the plane into the accumulators
+#pragma unroll
+        for (int j = 0; j < RY + K - 1; ++j) {
+            float win[RX + K - 1];
+            load_row<RX + K - 1, RX>(Fb + (ty * RY + j) * FP + tx * RX, win);
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                const int b = j - i;
+                if (b < 0 || b >= K) continue;
+#pragma unroll
+                for (int c = 0; c < K; ++c) {
+                    const int sl = Cfg::ROT ? (K - 1 - c) : (((u - c + R) % K + K) % K);
+#pragma unroll
+                    for (int x = 0; x < RX; ++x)
+#pragma unroll
+                        for (int a = 0; a < K; ++a)
+                            acc[sl][i][x] = fmaf(W.w[(c * K + b) * K + a], win[x + a], acc[sl][i][x]);
+                }
+            }
+        }
+        // output plane it - 2R + zc0 is complete
+        const int sl0 = Cfg::ROT ? 0 : (((u - R) % K + K) % K);
+        if (it >= 2 * R) {
+            const int oz = pfirst + it - R;
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                const int oy = y0 + ty * RY + i;
+                if (oy < p.ny && nvalid > 0) {
+                    const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
+                    store_row<RX>(p.dst, p.dfmt, idx, nvalid, acc[sl0][i], p.a0, p.a1, p.qmax);
+                }
+            }
+        }
+        if (Cfg::ROT) {
+#pragma unroll
+            for (int q = 0; q + 1 < K; ++q)
+#pragma unroll
+                for (int i = 0; i < RY; ++i)
+#pragma unroll
+                    for (int x = 0; x < RX; ++x) acc[q][i][x] = acc[q + 1][i][x];
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int x = 0; x < RX; ++x) acc[K - 1][i][x] = 0.f;
+        } else {
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int x = 0; x < RX; ++x) acc[sl0][i][x] = 0.f;
+        }
+    };
+
+    if (Cfg::ROT) {
+        for (int it = 0; it < nplanes && !failed; ++it) plane(it, 0);
+    } else {
+        for (int g = 0; g * K < nplanes && !failed; ++g) {
+#pragma unroll
+            for (int u = 0; u < K; ++u) {
+                const int it = g * K + u;
+                if (it >= nplanes || failed) break;
+                plane(it, u);
+            }
+        }
+    }
+
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(p.status, STATUS_TIMEOUT);
+            // drain loads still in flight (bounded) before the CTA's smem is released:
+            // the newest load issued to each stage completes that stage's current phase
+            for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
+                mbar_wait(&bars[it % STAGES], (it / STAGES) & 1);
+        }
+        __syncthreads();
+    }
+}
+
+template <int K>
+vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
+{
+    using Cfg = DirectCfg<K>;
+    using Geo = typename Cfg::Geo;
+    DirectArgs a;
+    a.src = job.src;
+    a.dst = job.dst;
+    a.nx = job.nx;
+    a.ny = job.ny;
+    a.nz = job.nz;
+    a.sfmt = job.sfmt;
+    a.dfmt = job.dfmt;
+    a.a0 = job.a0;
+    a.a1 = job.a1;
+    a.qmax = job.qmax;
+    a.status = ctx.status;
+    DenseW<K> W;
+    for (int i = 0; i < K * K * K; ++i) W.w[i] = w[i];
+
+    const int gx = (job.nx + Cfg::TX - 1) / Cfg::TX;
+    const int gy = (job.ny + Cfg::TY - 1) / Cfg::TY;
+    int sms = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long target = static_cast<long>(sms) * 8;   // ~2 waves of 4 CTAs per SM
+    const long xy = static_cast<long>(gx) * gy;
+    int chunks = static_cast<int>(std::min<long>((target + xy - 1) / xy, std::max(1, job.nz / 8)));
+    chunks = std::max(chunks, 1);
+    a.zchunk = (job.nz + chunks - 1) / chunks;
+    const int gz = (job.nz + a.zchunk - 1) / a.zchunk;
+
+    alignas(64) CUtensorMap map;
+    const int rawx = Geo::raw_w(job.sfmt);
+    a.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz, rawx,
+                                     Geo::FH, 1)
+                    ? 1
+                    : 0;
+    if (!a.use_tma) memset(&map, 0, sizeof(map));
+
+    const size_t smem = direct_smem_bytes<K>(job.sfmt);
+    cudaError_t e = cudaFuncSetAttribute(k_direct<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return from_cuda(e);
+    if (ctx.debug)
+        fprintf(stderr, "[vkt] direct k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n", K, gx,
+                gy, gz, a.zchunk, smem, a.use_tma);
+    k_direct<K><<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
+    count_launches(1);
+    return from_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx)
+{
+    switch (k) {
+    case 1: return launch_k<1>(job, w, ctx);
+    case 3: return launch_k<3>(job, w, ctx);
+    case 5: return launch_k<5>(job, w, ctx);
+    case 7: return launch_k<7>(job, w, ctx);
+    case 9: return launch_k<9>(job, w, ctx);
+    default: return VKT_ERROR_UNSUPPORTED;
+    }
+}
+
+}  // namespace vkt

@@ -1,0 +1,67 @@
+// vkt_internal.h -- host-side structures shared by the runtime and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vkt.h"
+
+#define VKT_VOLUME_MAGIC 0x564B5456u   // "VKTV"
+#define VKT_FILTER_MAGIC 0x564B5446u   // "VKTF"
+
+struct vktStructuredVolume_impl {
+    uint32_t magic;
+    void* data;          // device pointer
+    int owning;          // 1: cudaMalloc'ed by Create, freed by Destroy
+    int32_t dims[3];
+    vktDataFormat format;
+    float cell[3];
+    float lo, hi;
+};
+
+struct vktFilter_impl {
+    uint32_t magic;
+    int32_t k;
+    int separable;
+    float w[VKT_MAX_FILTER_SIZE * VKT_MAX_FILTER_SIZE * VKT_MAX_FILTER_SIZE];  // dense, x fastest
+    float g[3][VKT_MAX_FILTER_SIZE];   // separable vectors (x, y, z)
+};
+
+namespace vkt {
+
+// One filter application as the kernels see it.
+struct Job {
+    const void* src;
+    void* dst;
+    int nx, ny, nz;
+    int sfmt, dfmt;     // vktDataFormat values
+    // Epilogue: the kernels accumulate acc = sum w * q over stored source values q and
+    // write a0 + a1*acc (float dst), or clamp(rint(a0 + a1*acc), 0, qmax) (integer dst).
+    float a0, a1, qmax;
+};
+
+struct Ctx {
+    cudaStream_t stream;
+    int debug;
+    unsigned* status;   // device status word of the current device
+};
+
+// Kernel launchers (each returns VKT_NO_ERROR or a launch error).
+vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx);
+vktError launch_separable(const Job& job, const float* gx, const float* gy, const float* gz,
+                          int k, const Ctx& ctx);
+
+// Tensor-core path: VKT_NO_ERROR if it can evaluate this triple, else why not.
+vktError tensor_available(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                          const vktFilter_impl* f);
+vktError launch_tensor(const Job& job, const float* w, int k, const Ctx& ctx);
+
+// Helpers provided by the runtime.
+vktError get_context(Ctx* ctx);
+void count_launches(unsigned n);
+vktError from_cuda(cudaError_t e);
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+bool encode_tensor_map_3d(void* map /* CUtensorMap* */, int fmt, const void* base, int nx,
+                          int ny, int nz, int boxx, int boxy, int boxz);
+
+}  // namespace vkt

@@ -1,0 +1,624 @@
+// vkt_runtime.cu -- the C ABI of vkt.h: handles, thread-local execution policy, argument
+// validation, the value-mapping epilogue constants and the choice of evaluation path.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "vkt_internal.h"
+
+namespace vkt {
+
+namespace {
+
+thread_local vktExecutionPolicy t_policy = {nullptr, 0, 0, VKT_PATH_AUTO};
+std::atomic<uint64_t> g_launches{0};
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mutex;
+unsigned* g_status[MAX_DEVICES] = {};
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+bool g_encode_tried = false;
+
+bool valid(const vktStructuredVolume_impl* v) { return v && v->magic == VKT_VOLUME_MAGIC; }
+bool valid(const vktFilter_impl* f) { return f && f->magic == VKT_FILTER_MAGIC; }
+
+int fmt_bytes(vktDataFormat f) { return f == vktDataFormatUint8 ? 1 : (f == vktDataFormatUint16 ? 2 : 4); }
+double fmt_qmax(vktDataFormat f) { return f == vktDataFormatUint8 ? 255.0 : 65535.0; }
+bool fmt_valid(int f) { return f >= vktDataFormatUint8 && f <= vktDataFormatFloat32; }
+
+uint64_t volume_bytes(const vktStructuredVolume_impl* v)
+{
+    return static_cast<uint64_t>(v->dims[0]) * v->dims[1] * v->dims[2] * fmt_bytes(v->format);
+}
+
+vktError check_device()
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return VKT_ERROR_NO_DEVICE;
+    }
+    return VKT_NO_ERROR;
+}
+
+vktError check_volume_args(int32_t dx, int32_t dy, int32_t dz, vktDataFormat format, float sx,
+                           float sy, float sz, float lo, float hi)
+{
+    if (dx < 1 || dy < 1 || dz < 1) return VKT_ERROR_INVALID_VALUE;
+    if (!fmt_valid(format)) return VKT_ERROR_INVALID_VALUE;
+    if (!(sx > 0.f) || !(sy > 0.f) || !(sz > 0.f)) return VKT_ERROR_INVALID_VALUE;
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return VKT_ERROR_INVALID_VALUE;
+    if (format != vktDataFormatFloat32 && lo == hi) return VKT_ERROR_INVALID_VALUE;
+    return VKT_NO_ERROR;
+}
+
+vktError check_filter_size(int32_t k)
+{
+    if (k < 1 || k > VKT_MAX_FILTER_SIZE || (k & 1) == 0) return VKT_ERROR_UNSUPPORTED;
+    return VKT_NO_ERROR;
+}
+
+void dense_from_separable(vktFilter_impl* f)
+{
+    const int k = f->k;
+    for (int c = 0; c < k; ++c)
+        for (int b = 0; b < k; ++b)
+            for (int a = 0; a < k; ++a)
+                f->w[(c * k + b) * k + a] = static_cast<float>(
+                    static_cast<double>(f->g[2][c]) * f->g[1][b] * f->g[0][a]);
+}
+
+bool overlaps(const vktStructuredVolume_impl* a, const vktStructuredVolume_impl* b)
+{
+    const char* pa = static_cast<const char*>(a->data);
+    const char* pb = static_cast<const char*>(b->data);
+    return pa < pb + volume_bytes(b) && pb < pa + volume_bytes(a);
+}
+
+// Epilogue constants of one (dst, src, filter-sum) triple.  The kernels accumulate over
+// stored values q (codes for integer sources); the mapped result is
+//   v = lo_s * W + s_s * acc,   W = sum of the weights, s_s = (hi_s - lo_s)/(2^N - 1)
+// and an integer destination stores clamp(rint((v - lo_d) * (2^M - 1)/(hi_d - lo_d))).
+void epilogue(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+              double wsum, Job* job)
+{
+    double ls = 0.0, ss = 1.0;
+    if (src->format != vktDataFormatFloat32) {
+        ls = src->lo;
+        ss = (static_cast<double>(src->hi) - src->lo) / fmt_qmax(src->format);
+    }
+    if (dst->format == vktDataFormatFloat32) {
+        job->a0 = static_cast<float>(ls * wsum);
+        job->a1 = static_cast<float>(ss);
+        job->qmax = 0.f;
+    } else {
+        const double sd = fmt_qmax(dst->format) / (static_cast<double>(dst->hi) - dst->lo);
+        job->a0 = static_cast<float>((ls * wsum - dst->lo) * sd);
+        job->a1 = static_cast<float>(ss * sd);
+        job->qmax = static_cast<float>(fmt_qmax(dst->format));
+    }
+}
+
+}  // namespace
+
+vktError get_context(Ctx* ctx)
+{
+    vktError err = check_device();
+    if (err != VKT_NO_ERROR) return err;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return VKT_ERROR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_status[dev]) {
+            unsigned* p = nullptr;
+            e = cudaMalloc(&p, 16);
+            if (e != cudaSuccess) return from_cuda(e);
+            e = cudaMemset(p, 0, 16);
+            if (e != cudaSuccess) {
+                cudaFree(p);
+                return from_cuda(e);
+            }
+            g_status[dev] = p;
+        }
+        ctx->status = g_status[dev];
+    }
+    ctx->stream = static_cast<cudaStream_t>(t_policy.stream);
+    ctx->debug = t_policy.debug;
+    return VKT_NO_ERROR;
+}
+
+void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+vktError from_cuda(cudaError_t e)
+{
+    switch (e) {
+    case cudaSuccess: return VKT_NO_ERROR;
+    case cudaErrorMemoryAllocation: cudaGetLastError(); return VKT_ERROR_OUT_OF_MEMORY;
+    case cudaErrorNoDevice:
+    case cudaErrorInsufficientDriver: cudaGetLastError(); return VKT_ERROR_NO_DEVICE;
+    default: cudaGetLastError(); return VKT_ERROR_CUDA;
+    }
+}
+
+bool encode_tensor_map_3d(void* map, int fmt, const void* base, int nx, int ny, int nz,
+                          int boxx, int boxy, int boxz)
+{
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_encode_tried) {
+            g_encode_tried = true;
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                 cudaEnableDefault, &q) == cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+            cudaGetLastError();
+        }
+    }
+    if (!g_encode) return false;
+    const int es = fmt == vktDataFormatUint8 ? 1 : (fmt == vktDataFormatUint16 ? 2 : 4);
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    if ((static_cast<uint64_t>(nx) * es) % 16 != 0) return false;
+    if (boxx > 256 || boxy > 256 || boxz > 256 || (boxx * es) % 16 != 0) return false;
+    const CUtensorMapDataType dt = fmt == vktDataFormatUint8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                   : fmt == vktDataFormatUint16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
+                          static_cast<cuuint64_t>(nz)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * es,
+                             static_cast<cuuint64_t>(nx) * ny * es};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(boxx), static_cast<cuuint32_t>(boxy),
+                         static_cast<cuuint32_t>(boxz)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(static_cast<CUtensorMap*>(map), dt, 3, const_cast<void*>(base), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace vkt
+
+using namespace vkt;
+
+extern "C" {
+
+vktError vktSetThreadExecutionPolicy(vktExecutionPolicy policy)
+{
+    if (policy.path < VKT_PATH_AUTO || policy.path > VKT_PATH_TENSOR) return VKT_ERROR_INVALID_VALUE;
+    t_policy = policy;
+    return VKT_NO_ERROR;
+}
+
+vktError vktGetThreadExecutionPolicy(vktExecutionPolicy* policy)
+{
+    if (!policy) return VKT_ERROR_INVALID_VALUE;
+    *policy = t_policy;
+    return VKT_NO_ERROR;
+}
+
+const char* vktGetErrorString(vktError error)
+{
+    switch (error) {
+    case VKT_NO_ERROR: return "no error";
+    case VKT_ERROR_INVALID_VALUE: return "invalid value";
+    case VKT_ERROR_INVALID_HANDLE: return "invalid handle";
+    case VKT_ERROR_DIMS_MISMATCH: return "volume dims mismatch";
+    case VKT_ERROR_UNSUPPORTED: return "unsupported filter size, format or path";
+    case VKT_ERROR_OUT_OF_MEMORY: return "out of device memory";
+    case VKT_ERROR_NO_DEVICE: return "no CUDA device";
+    case VKT_ERROR_CUDA: return "CUDA error";
+    case VKT_ERROR_DEVICE_TIMEOUT: return "a bounded device wait timed out";
+    default: return "unknown error";
+    }
+}
+
+vktError vktSynchronize(void)
+{
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+    cudaError_t e = cudaStreamSynchronize(ctx.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    unsigned st = 0;
+    e = cudaMemcpyAsync(&st, ctx.status, sizeof(st), cudaMemcpyDeviceToHost, ctx.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (st != 0) {
+        e = cudaMemsetAsync(ctx.status, 0, sizeof(st), ctx.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        return VKT_ERROR_DEVICE_TIMEOUT;
+    }
+    return VKT_NO_ERROR;
+}
+
+vktError vktGetLaunchCount(uint64_t* count)
+{
+    if (!count) return VKT_ERROR_INVALID_VALUE;
+    *count = g_launches.load();
+    return VKT_NO_ERROR;
+}
+
+// ------------------------------------------------------------------ volumes
+
+static vktError create_volume(vktStructuredVolume* volume, void* devPtr, int owning, int32_t dx,
+                              int32_t dy, int32_t dz, vktDataFormat format, float sx, float sy,
+                              float sz, float lo, float hi)
+{
+    if (!volume) return VKT_ERROR_INVALID_VALUE;
+    *volume = nullptr;
+    vktError err = check_volume_args(dx, dy, dz, format, sx, sy, sz, lo, hi);
+    if (err != VKT_NO_ERROR) return err;
+    if (!owning && (!devPtr || reinterpret_cast<uintptr_t>(devPtr) % fmt_bytes(format) != 0))
+        return VKT_ERROR_INVALID_VALUE;
+    auto* v = new (std::nothrow) vktStructuredVolume_impl;
+    if (!v) return VKT_ERROR_OUT_OF_MEMORY;
+    v->magic = VKT_VOLUME_MAGIC;
+    v->dims[0] = dx;
+    v->dims[1] = dy;
+    v->dims[2] = dz;
+    v->format = format;
+    v->cell[0] = sx;
+    v->cell[1] = sy;
+    v->cell[2] = sz;
+    v->lo = lo;
+    v->hi = hi;
+    v->owning = owning;
+    v->data = devPtr;
+    if (owning) {
+        err = check_device();
+        if (err == VKT_NO_ERROR) {
+            cudaError_t e = cudaMalloc(&v->data, volume_bytes(v));
+            if (e == cudaSuccess) e = cudaMemset(v->data, 0, volume_bytes(v));
+            err = from_cuda(e);
+        }
+        if (err != VKT_NO_ERROR) {
+            if (v->data) cudaFree(v->data);
+            v->magic = 0;
+            delete v;
+            return err;
+        }
+    }
+    *volume = v;
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeCreate(vktStructuredVolume* volume, int32_t dx, int32_t dy,
+                                   int32_t dz, vktDataFormat format, float sx, float sy,
+                                   float sz, float lo, float hi)
+{
+    return create_volume(volume, nullptr, 1, dx, dy, dz, format, sx, sy, sz, lo, hi);
+}
+
+vktError vktStructuredVolumeCreateView(vktStructuredVolume* volume, void* devPtr, int32_t dx,
+                                       int32_t dy, int32_t dz, vktDataFormat format, float sx,
+                                       float sy, float sz, float lo, float hi)
+{
+    return create_volume(volume, devPtr, 0, dx, dy, dz, format, sx, sy, sz, lo, hi);
+}
+
+vktError vktStructuredVolumeDestroy(vktStructuredVolume volume)
+{
+    if (!valid(volume)) return VKT_ERROR_INVALID_HANDLE;
+    vktError err = VKT_NO_ERROR;
+    if (volume->owning && volume->data) err = from_cuda(cudaFree(volume->data));
+    volume->magic = 0;
+    delete volume;
+    return err;
+}
+
+vktError vktStructuredVolumeGetDims(vktStructuredVolume v, int32_t* dx, int32_t* dy, int32_t* dz)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!dx || !dy || !dz) return VKT_ERROR_INVALID_VALUE;
+    *dx = v->dims[0];
+    *dy = v->dims[1];
+    *dz = v->dims[2];
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeGetDataFormat(vktStructuredVolume v, vktDataFormat* format)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!format) return VKT_ERROR_INVALID_VALUE;
+    *format = v->format;
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeGetCellSize(vktStructuredVolume v, float* sx, float* sy, float* sz)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!sx || !sy || !sz) return VKT_ERROR_INVALID_VALUE;
+    *sx = v->cell[0];
+    *sy = v->cell[1];
+    *sz = v->cell[2];
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeGetVoxelMapping(vktStructuredVolume v, float* lo, float* hi)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!lo || !hi) return VKT_ERROR_INVALID_VALUE;
+    *lo = v->lo;
+    *hi = v->hi;
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeSetVoxelMapping(vktStructuredVolume v, float lo, float hi)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!std::isfinite(lo) || !std::isfinite(hi)) return VKT_ERROR_INVALID_VALUE;
+    if (v->format != vktDataFormatFloat32 && lo == hi) return VKT_ERROR_INVALID_VALUE;
+    v->lo = lo;
+    v->hi = hi;
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeGetData(vktStructuredVolume v, void** devPtr)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!devPtr) return VKT_ERROR_INVALID_VALUE;
+    *devPtr = v->data;
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeGetSizeInBytes(vktStructuredVolume v, uint64_t* bytes)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!bytes) return VKT_ERROR_INVALID_VALUE;
+    *bytes = volume_bytes(v);
+    return VKT_NO_ERROR;
+}
+
+vktError vktStructuredVolumeSetData(vktStructuredVolume v, const void* hostPtr)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!hostPtr) return VKT_ERROR_INVALID_VALUE;
+    vktError err = check_device();
+    if (err != VKT_NO_ERROR) return err;
+    return from_cuda(cudaMemcpyAsync(v->data, hostPtr, volume_bytes(v), cudaMemcpyHostToDevice,
+                                     static_cast<cudaStream_t>(t_policy.stream)));
+}
+
+vktError vktStructuredVolumeCopyToHost(vktStructuredVolume v, void* hostPtr)
+{
+    if (!valid(v)) return VKT_ERROR_INVALID_HANDLE;
+    if (!hostPtr) return VKT_ERROR_INVALID_VALUE;
+    vktError err = check_device();
+    if (err != VKT_NO_ERROR) return err;
+    return from_cuda(cudaMemcpyAsync(hostPtr, v->data, volume_bytes(v), cudaMemcpyDeviceToHost,
+                                     static_cast<cudaStream_t>(t_policy.stream)));
+}
+
+// ------------------------------------------------------------------ filters
+
+static vktFilter_impl* new_filter(int32_t k)
+{
+    auto* f = new (std::nothrow) vktFilter_impl;
+    if (!f) return nullptr;
+    memset(f, 0, sizeof(*f));
+    f->magic = VKT_FILTER_MAGIC;
+    f->k = k;
+    return f;
+}
+
+vktError vktFilterCreate(vktFilter* filter, int32_t k, const float* hostWeights)
+{
+    if (!filter) return VKT_ERROR_INVALID_VALUE;
+    *filter = nullptr;
+    vktError err = check_filter_size(k);
+    if (err != VKT_NO_ERROR) return err;
+    vktFilter_impl* f = new_filter(k);
+    if (!f) return VKT_ERROR_OUT_OF_MEMORY;
+    if (hostWeights) memcpy(f->w, hostWeights, sizeof(float) * k * k * k);
+    *filter = f;
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterCreateSeparable(vktFilter* filter, int32_t k, const float* wx, const float* wy,
+                                  const float* wz)
+{
+    if (!filter) return VKT_ERROR_INVALID_VALUE;
+    *filter = nullptr;
+    vktError err = check_filter_size(k);
+    if (err != VKT_NO_ERROR) return err;
+    if (!wx || !wy || !wz) return VKT_ERROR_INVALID_VALUE;
+    vktFilter_impl* f = new_filter(k);
+    if (!f) return VKT_ERROR_OUT_OF_MEMORY;
+    f->separable = 1;
+    memcpy(f->g[0], wx, sizeof(float) * k);
+    memcpy(f->g[1], wy, sizeof(float) * k);
+    memcpy(f->g[2], wz, sizeof(float) * k);
+    dense_from_separable(f);
+    *filter = f;
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterCreateGaussian(vktFilter* filter, int32_t k, float sigma)
+{
+    if (!filter) return VKT_ERROR_INVALID_VALUE;
+    *filter = nullptr;
+    vktError err = check_filter_size(k);
+    if (err != VKT_NO_ERROR) return err;
+    if (!(sigma > 0.f) || !std::isfinite(sigma)) return VKT_ERROR_INVALID_VALUE;
+    // sampled Gaussian at integer offsets, normalised by its FP64 sum
+    const int r = (k - 1) / 2;
+    double e[VKT_MAX_FILTER_SIZE], s = 0.0;
+    const double sg = sigma;
+    for (int i = 0; i < k; ++i) {
+        const double d = static_cast<double>(i - r);
+        e[i] = std::exp(-d * d / (2.0 * sg * sg));
+        s += e[i];
+    }
+    float g[VKT_MAX_FILTER_SIZE];
+    for (int i = 0; i < k; ++i) g[i] = static_cast<float>(e[i] / s);
+    return vktFilterCreateSeparable(filter, k, g, g, g);
+}
+
+vktError vktFilterSetWeights(vktFilter f, const float* hostWeights)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    if (!hostWeights) return VKT_ERROR_INVALID_VALUE;
+    memcpy(f->w, hostWeights, sizeof(float) * f->k * f->k * f->k);
+    f->separable = 0;
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterNormalize(vktFilter f)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    const int k = f->k;
+    if (f->separable) {
+        double sums[3];
+        for (int a = 0; a < 3; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < k; ++i) s += f->g[a][i];
+            if (s == 0.0 || !std::isfinite(s)) return VKT_ERROR_INVALID_VALUE;
+            sums[a] = s;
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < k; ++i) f->g[a][i] = static_cast<float>(f->g[a][i] / sums[a]);
+        dense_from_separable(f);
+        return VKT_NO_ERROR;
+    }
+    double s = 0.0;
+    for (int i = 0; i < k * k * k; ++i) s += f->w[i];
+    if (s == 0.0 || !std::isfinite(s)) return VKT_ERROR_INVALID_VALUE;
+    for (int i = 0; i < k * k * k; ++i) f->w[i] = static_cast<float>(f->w[i] / s);
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterGetSize(vktFilter f, int32_t* k)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    if (!k) return VKT_ERROR_INVALID_VALUE;
+    *k = f->k;
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterIsSeparable(vktFilter f, int32_t* separable)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    if (!separable) return VKT_ERROR_INVALID_VALUE;
+    *separable = f->separable;
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterGetWeights(vktFilter f, float* hostWeights)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    if (!hostWeights) return VKT_ERROR_INVALID_VALUE;
+    memcpy(hostWeights, f->w, sizeof(float) * f->k * f->k * f->k);
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterGetSeparableWeights(vktFilter f, float* wx, float* wy, float* wz)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    if (!wx || !wy || !wz) return VKT_ERROR_INVALID_VALUE;
+    if (!f->separable) return VKT_ERROR_UNSUPPORTED;
+    memcpy(wx, f->g[0], sizeof(float) * f->k);
+    memcpy(wy, f->g[1], sizeof(float) * f->k);
+    memcpy(wz, f->g[2], sizeof(float) * f->k);
+    return VKT_NO_ERROR;
+}
+
+vktError vktFilterDestroy(vktFilter f)
+{
+    if (!valid(f)) return VKT_ERROR_INVALID_HANDLE;
+    f->magic = 0;
+    delete f;
+    return VKT_NO_ERROR;
+}
+
+// ------------------------------------------------------------------ ApplyFilter
+
+vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter)
+{
+    if (!valid(dst) || !valid(src) || !valid(filter)) return VKT_ERROR_INVALID_HANDLE;
+    if (dst->dims[0] != src->dims[0] || dst->dims[1] != src->dims[1] ||
+        dst->dims[2] != src->dims[2])
+        return VKT_ERROR_DIMS_MISMATCH;
+    if (overlaps(dst, src)) return VKT_ERROR_INVALID_VALUE;
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+
+    const int k = filter->k;
+    int path = t_policy.path;
+    if (path == VKT_PATH_AUTO) {
+        if (filter->separable)
+            path = VKT_PATH_SEPARABLE;
+        else if (k >= 5 && tensor_available(dst, src, filter) == VKT_NO_ERROR)
+            path = VKT_PATH_TENSOR;
+        else
+            path = VKT_PATH_DIRECT;
+    }
+    if (path == VKT_PATH_SEPARABLE && !filter->separable) return VKT_ERROR_UNSUPPORTED;
+    if (path == VKT_PATH_TENSOR) {
+        err = tensor_available(dst, src, filter);
+        if (err != VKT_NO_ERROR) return err;
+    }
+
+    Job job;
+    job.src = src->data;
+    job.dst = dst->data;
+    job.nx = src->dims[0];
+    job.ny = src->dims[1];
+    job.nz = src->dims[2];
+    job.sfmt = src->format;
+    job.dfmt = dst->format;
+    double wsum = 0.0;
+    if (path == VKT_PATH_SEPARABLE) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < k; ++i) s[a] += filter->g[a][i];
+        wsum = s[0] * s[1] * s[2];
+    } else {
+        for (int i = 0; i < k * k * k; ++i) wsum += filter->w[i];
+    }
+    epilogue(dst, src, wsum, &job);
+
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (t_policy.printTimes) {
+        cudaEventCreate(&ev[0]);
+        cudaEventCreate(&ev[1]);
+        cudaEventRecord(ev[0], ctx.stream);
+    }
+    if (path == VKT_PATH_SEPARABLE)
+        err = launch_separable(job, filter->g[0], filter->g[1], filter->g[2], k, ctx);
+    else if (path == VKT_PATH_TENSOR)
+        err = launch_tensor(job, filter->w, k, ctx);
+    else
+        err = launch_direct(job, filter->w, k, ctx);
+    if (t_policy.printTimes) {
+        cudaEventRecord(ev[1], ctx.stream);
+        cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        fprintf(stderr, "[vkt] ApplyFilter %dx%dx%d k=%d path=%d: %.3f ms\n", job.nx, job.ny,
+                job.nz, k, path, ms);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    return err;
+}
+
+}  // extern "C"

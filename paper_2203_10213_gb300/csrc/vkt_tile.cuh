@@ -1,0 +1,263 @@
+// vkt_tile.cuh -- device helpers shared by the filter kernels: mbarrier and TMA wrappers
+// (inline PTX, sm_103a), bounded waits, brick geometry, the raw-tile to float-tile
+// conversion with clamp-to-edge, and the output epilogue.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vkt {
+
+enum : int { FMT_U8 = 0, FMT_U16 = 1, FMT_F32 = 2 };
+
+constexpr unsigned STATUS_TIMEOUT = 1u;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s for any single device wait
+
+__host__ __device__ constexpr int fmt_bytes(int f) { return f == FMT_U8 ? 1 : (f == FMT_U16 ? 2 : 4); }
+// TMA needs the innermost start coordinate on a 16-byte boundary: x halo per side
+__host__ __device__ constexpr int fmt_xalign(int f) { return 16 / fmt_bytes(f); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of `parity` to complete; false after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return true;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensor_map(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// Geometry of one brick plane: TX x TY outputs, radius R, float tile of (TY+2R) rows
+// starting at (x0-R, y0-R), pitch a multiple of 4 floats.  The raw tile (what TMA
+// writes) starts at (x0 - XA, y0 - R), with XA = 16 bytes / voxel size >= R.
+template <int K, int TX, int TY>
+struct Brick {
+    static constexpr int R = (K - 1) / 2;
+    static constexpr int FW = TX + 2 * R;
+    static constexpr int FP = (FW + 3) & ~3;
+    static constexpr int FH = TY + 2 * R;
+    static constexpr int FGROUPS = FP / 4;          // float4 groups per row
+    static_assert(R <= 4, "x halo of a float32 raw tile is 4 voxels");
+    __host__ __device__ static constexpr int raw_w(int fmt) { return TX + 2 * fmt_xalign(fmt); }
+    // bytes one TMA box delivers, and the (128-byte padded) size of one raw stage
+    __host__ __device__ static constexpr int raw_tx(int fmt) { return raw_w(fmt) * FH * fmt_bytes(fmt); }
+    __host__ __device__ static constexpr int raw_bytes(int fmt) { return (raw_tx(fmt) + 127) & ~127; }
+};
+
+__device__ __forceinline__ float load_raw(const unsigned char* raw, int fmt, int idx)
+{
+    if (fmt == FMT_F32) return reinterpret_cast<const float*>(raw)[idx];
+    if (fmt == FMT_U16) return static_cast<float>(reinterpret_cast<const uint16_t*>(raw)[idx]);
+    return static_cast<float>(raw[idx]);
+}
+
+__device__ __forceinline__ float load_global(const void* src, int fmt, int64_t idx)
+{
+    if (fmt == FMT_F32) return __ldg(reinterpret_cast<const float*>(src) + idx);
+    if (fmt == FMT_U16) return static_cast<float>(__ldg(reinterpret_cast<const uint16_t*>(src) + idx));
+    return static_cast<float>(__ldg(reinterpret_cast<const unsigned char*>(src) + idx));
+}
+
+// Fills the raw tile of plane z with plain loads at clamped coordinates (the path for
+// volumes whose rows cannot be described by a tensor map).  Positions outside the
+// volume receive the clamped neighbour, which the conversion never reads anyway.
+template <typename Geo, int NT>
+__device__ __forceinline__ void fill_raw_plain(unsigned char* raw, const void* src, int fmt,
+                                               int nx, int ny, int x0, int y0, int z, int tid)
+{
+    const int xa = fmt_xalign(fmt);
+    const int rw = Geo::raw_w(fmt);
+    const int n = rw * Geo::FH;
+    const int64_t plane = static_cast<int64_t>(z) * nx * ny;
+    for (int e = tid; e < n; e += NT) {
+        const int row = e / rw, col = e - row * rw;
+        const int gy = clampi(y0 - Geo::R + row, 0, ny - 1);
+        const int gx = clampi(x0 - xa + col, 0, nx - 1);
+        const int64_t gi = plane + static_cast<int64_t>(gy) * nx + gx;
+        if (fmt == FMT_F32)
+            reinterpret_cast<float*>(raw)[e] = __ldg(reinterpret_cast<const float*>(src) + gi);
+        else if (fmt == FMT_U16)
+            reinterpret_cast<uint16_t*>(raw)[e] = __ldg(reinterpret_cast<const uint16_t*>(src) + gi);
+        else
+            raw[e] = __ldg(reinterpret_cast<const unsigned char*>(src) + gi);
+    }
+}
+
+// Per-thread precomputed raw-tile offsets of the float-tile groups this thread converts.
+// Group gi covers float-tile row gi / FGROUPS, columns 4*(gi % FGROUPS) .. +3; each of
+// its 4 elements reads the raw tile at the clamped voxel position.
+template <typename Geo, int NT>
+struct ConvPlan {
+    static constexpr int NG = (Geo::FH * Geo::FGROUPS + NT - 1) / NT;
+    int off[NG][4];
+
+    __device__ __forceinline__ void init(int fmt, int nx, int ny, int x0, int y0, int tid)
+    {
+        const int xa = fmt_xalign(fmt);
+        const int rw = Geo::raw_w(fmt);
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            const int gi = tid + n * NT;
+            const int row = gi / Geo::FGROUPS;
+            const int g = gi - row * Geo::FGROUPS;
+            const int gy = clampi(y0 - Geo::R + row, 0, ny - 1);
+            const int rrow = gy - (y0 - Geo::R);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                // padding columns past the halo repeat the last halo column
+                const int j = min(4 * g + e, Geo::FW - 1);
+                const int gx = clampi(x0 - Geo::R + j, 0, nx - 1);
+                off[n][e] = rrow * rw + (gx - (x0 - xa));
+            }
+        }
+    }
+
+    // raw tile -> float tile (pitch FP), every element mapped to its clamped voxel
+    __device__ __forceinline__ void convert(const unsigned char* raw, int fmt, float* F,
+                                            int tid) const
+    {
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            const int gi = tid + n * NT;
+            if (NG * NT > Geo::FH * Geo::FGROUPS && gi >= Geo::FH * Geo::FGROUPS) break;
+            float4 v;
+            if (fmt == FMT_F32) {
+                const float* r = reinterpret_cast<const float*>(raw);
+                v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
+            } else if (fmt == FMT_U16) {
+                const uint16_t* r = reinterpret_cast<const uint16_t*>(raw);
+                v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
+            } else {
+                v = make_float4(raw[off[n][0]], raw[off[n][1]], raw[off[n][2]], raw[off[n][3]]);
+            }
+            reinterpret_cast<float4*>(F)[gi] = v;
+        }
+    }
+};
+
+// Loads N consecutive floats from shared memory aligned to VEC floats (VEC = 1, 2 or 4).
+template <int N, int VEC>
+__device__ __forceinline__ void load_row(const float* p, float (&v)[N])
+{
+    constexpr int N4 = (VEC == 4) ? (N / 4) * 4 : 0;
+#pragma unroll
+    for (int i = 0; i < N4; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p + i);
+        v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
+    }
+    constexpr int N2 = (VEC >= 2) ? N4 + ((N - N4) / 2) * 2 : 0;
+#pragma unroll
+    for (int i = N4; i < N2; i += 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p + i);
+        v[i] = t.x; v[i + 1] = t.y;
+    }
+#pragma unroll
+    for (int i = N2; i < N; ++i) v[i] = p[i];
+}
+
+// Writes RX consecutive results of one row, mapped to the destination format.
+template <int RX>
+__device__ __forceinline__ void store_row(void* dst, int dfmt, int64_t idx, int nvalid,
+                                          const float (&acc)[RX], float a0, float a1, float qmax)
+{
+    float v[RX];
+#pragma unroll
+    for (int x = 0; x < RX; ++x) v[x] = fmaf(a1, acc[x], a0);
+    if (dfmt == FMT_F32) {
+        float* d = reinterpret_cast<float*>(dst) + idx;
+        if (RX == 4 && nvalid >= 4 && (idx & 3) == 0) {
+            *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
+        } else if (RX == 2 && nvalid >= 2 && (idx & 1) == 0) {
+            *reinterpret_cast<float2*>(d) = make_float2(v[0], v[1]);
+        } else {
+#pragma unroll
+            for (int x = 0; x < RX; ++x)
+                if (x < nvalid) d[x] = v[x];
+        }
+        return;
+    }
+    unsigned q[RX];
+#pragma unroll
+    for (int x = 0; x < RX; ++x) q[x] = static_cast<unsigned>(fminf(fmaxf(rintf(v[x]), 0.f), qmax));
+    if (dfmt == FMT_U16) {
+        uint16_t* d = reinterpret_cast<uint16_t*>(dst) + idx;
+#pragma unroll
+        for (int x = 0; x < RX; ++x)
+            if (x < nvalid) d[x] = static_cast<uint16_t>(q[x]);
+    } else {
+        unsigned char* d = reinterpret_cast<unsigned char*>(dst) + idx;
+#pragma unroll
+        for (int x = 0; x < RX; ++x)
+            if (x < nvalid) d[x] = static_cast<unsigned char>(q[x]);
+    }
+}
+
+}  // namespace vkt

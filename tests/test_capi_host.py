@@ -1,0 +1,159 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every symbol the
+header declares, validates its arguments, and builds filters as documented."""
+import ctypes
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vkt.h")
+
+
+@pytest.fixture(scope="module")
+def vkt():
+    import paper_2203_10213_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def lib(vkt):
+    return vkt._lib
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_2203_10213_gb300._lib import SIGNATURES, declared_symbols
+    names = declared_symbols(HEADER)
+    assert len(names) >= 30
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in vkt.h but not exported"
+        assert name in SIGNATURES, f"{name} has no Python binding"
+    # and nothing beyond the vkt* API leaks out of the shared library
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], capture_output=True, text=True)
+    if out.returncode == 0:
+        exported = {ln.split()[-1] for ln in out.stdout.splitlines() if " T " in ln}
+        assert {n for n in exported if n.startswith("vkt")} == set(names)
+
+
+def test_error_strings(lib):
+    for code in range(9):
+        assert lib.vktGetErrorString(code)
+    assert lib.vktGetErrorString(99) == b"unknown error"
+
+
+def test_policy_roundtrip(vkt, lib):
+    pol = vkt.ExecutionPolicy()
+    pol.stream = None
+    pol.printTimes = 1
+    pol.debug = 0
+    pol.path = vkt.PATH_DIRECT
+    assert lib.vktSetThreadExecutionPolicy(pol) == 0
+    got = vkt.ExecutionPolicy()
+    assert lib.vktGetThreadExecutionPolicy(ctypes.byref(got)) == 0
+    assert (got.printTimes, got.path) == (1, vkt.PATH_DIRECT)
+    pol.path = 17
+    assert lib.vktSetThreadExecutionPolicy(pol) == 1
+    pol.path = 0
+    pol.printTimes = 0
+    assert lib.vktSetThreadExecutionPolicy(pol) == 0
+
+
+def test_volume_argument_validation(vkt, lib):
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x10000)
+    cv = lib.vktStructuredVolumeCreateView
+    assert cv(None, fake, 4, 4, 4, vkt.F32, 1, 1, 1, 0, 1) == 1
+    assert cv(ctypes.byref(h), None, 4, 4, 4, vkt.F32, 1, 1, 1, 0, 1) == 1
+    assert cv(ctypes.byref(h), fake, 0, 4, 4, vkt.F32, 1, 1, 1, 0, 1) == 1
+    assert cv(ctypes.byref(h), fake, 4, 4, 4, 7, 1, 1, 1, 0, 1) == 1
+    assert cv(ctypes.byref(h), fake, 4, 4, 4, vkt.U8, 1, 1, 1, 0.5, 0.5) == 1   # lo == hi
+    assert cv(ctypes.byref(h), fake, 4, 4, 4, vkt.F32, 0, 1, 1, 0, 1) == 1      # cell size
+    assert cv(ctypes.byref(h), ctypes.c_void_p(0x10001), 4, 4, 4, vkt.F32, 1, 1, 1, 0, 1) == 1
+    # a valid view needs no device: it only records the pointer
+    assert cv(ctypes.byref(h), fake, 5, 6, 7, vkt.U16, 1, 2, 3, -1, 2) == 0
+    v = vkt.StructuredVolume(h)
+    assert v.dims == (5, 6, 7)
+    assert v.format == vkt.U16
+    assert v.cell_size == (1.0, 2.0, 3.0)
+    assert v.mapping == (-1.0, 2.0)
+    assert v.nbytes == 5 * 6 * 7 * 2
+    assert v.data_ptr == 0x10000
+    v.set_mapping(0.0, 4.0)
+    assert v.mapping == (0.0, 4.0)
+    with pytest.raises(vkt.VktError):
+        v.set_mapping(1.0, 1.0)
+    v.destroy()
+    assert lib.vktStructuredVolumeDestroy(None) == 2
+
+
+def test_apply_filter_validation_without_device(vkt, lib):
+    fake1, fake2 = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
+    a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(a), fake1, 8, 8, 8, vkt.F32, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(b), fake2, 8, 8, 9, vkt.F32, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(c), ctypes.c_void_p(0x100100), 8, 8, 8,
+                                             vkt.F32, 1, 1, 1, 0, 1) == 0
+    f = vkt.Filter.gaussian(3, 1.0)
+    assert lib.vktApplyFilterSV(None, a, f.handle) == 2
+    assert lib.vktApplyFilterSV(a, b, f.handle) == 3          # dims mismatch
+    assert lib.vktApplyFilterSV(a, c, f.handle) == 1          # overlapping memory
+    for h in (a, b, c):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
+def test_owning_create_reports_missing_device(vkt, lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    h = ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreate(ctypes.byref(h), 4, 4, 4, vkt.F32, 1, 1, 1, 0, 1) == 6
+
+
+def test_filter_validation(vkt, lib):
+    h = ctypes.c_void_p()
+    for k in (0, 2, 4, 11, -1):
+        assert lib.vktFilterCreate(ctypes.byref(h), k, None) == 4
+    assert lib.vktFilterCreateGaussian(ctypes.byref(h), 3, 0.0) == 1
+    assert lib.vktFilterCreateGaussian(ctypes.byref(h), 3, -1.0) == 1
+    f = vkt.Filter.dense(np.zeros((3, 3, 3)))
+    assert not f.is_separable
+    with pytest.raises(vkt.VktError):
+        f.normalize()                      # zero sum
+    with pytest.raises(vkt.VktError):
+        f.separable_weights()
+    assert lib.vktFilterDestroy(None) == 2
+
+
+@pytest.mark.parametrize("k,sigma", [(3, 1.0), (5, 1.5), (7, 7 / 3), (9, 3.0)])
+def test_gaussian_filter_matches_oracle_construction(vkt, k, sigma):
+    sigma = float(np.float32(sigma))      # the C ABI takes sigma as a float
+    f = vkt.Filter.gaussian(k, sigma)
+    assert f.k == k and f.is_separable
+    gx, gy, gz = f.separable_weights()
+    g = oracle.gaussian_1d(k, sigma)
+    assert np.array_equal(gx, g) and np.array_equal(gy, g) and np.array_equal(gz, g)
+    dense = f.weights()
+    assert np.allclose(dense, oracle.gaussian_weights(k, sigma), rtol=1e-6, atol=0)
+
+
+def test_dense_roundtrip_and_normalize(vkt):
+    w = np.arange(27, dtype=np.float32).reshape(3, 3, 3) + 1
+    f = vkt.Filter.dense(w)
+    assert np.array_equal(f.weights(), w)
+    f.normalize()
+    assert math.isclose(float(f.weights().astype(np.float64).sum()), 1.0, rel_tol=1e-6)
+    np.testing.assert_allclose(f.weights(), (w / w.astype(np.float64).sum()).astype(np.float32))
+    f.set_weights(w * 2)
+    assert np.array_equal(f.weights(), w * 2)
+
+
+def test_separable_normalize_each_vector(vkt):
+    f = vkt.Filter.separable([1, 2, 1], [1, 1, 1], [0, 4, 0])
+    f.normalize()
+    gx, gy, gz = f.separable_weights()
+    assert np.allclose(gx, [0.25, 0.5, 0.25]) and np.allclose(gy, 1 / 3) and np.allclose(gz, [0, 1, 0])
+    assert np.allclose(f.weights().sum(), 1.0)

@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="skip the tensor-core vs FP32 comparison on the 1024x1024x512 field")
+    ap.add_argument("--precision-reps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -124,23 +127,89 @@ def workload_host():
 
 
 def oracle_sample_rate(vol, seconds: float, seed: int = 7):
-    """Times the FP64 oracle on random voxels of the workload; returns voxels/s (both
-    filters, each output counted once) and the sample description."""
+    """Times the FP64 oracle on random voxels of the workload for about `seconds`; returns
+    voxels/s (both filters, each output counted once), the voxel count and the time."""
     import oracle
     w_g = oracle.gaussian_weights(5, float(np.float32(1.5)))
     w_l = oracle.laplacian_3()
     rng = np.random.default_rng(seed)
-    n = 4096
-    while True:
+    n, total_n, total_t = 4096, 0, 0.0
+    while total_t < seconds:
         idx = rng.integers(0, vol.size, n)
         t0 = time.perf_counter()
         oracle.correlate_points(vol, w_g, idx, 0.0, 1.0)
         oracle.correlate_points(vol, w_l, idx, 0.0, 1.0)
         dt = time.perf_counter() - t0
-        if dt >= seconds or n >= 1 << 26:
-            break
-        n = int(min(n * max(2.0, seconds / max(dt, 1e-3)), 1 << 26))
-    return 2 * n / dt, n, dt
+        total_n += n
+        total_t += dt
+        rate = n / max(dt, 1e-6)
+        n = int(min(max(4096, rate * (seconds - total_t)), 1 << 24))
+    return 2 * total_n / total_t, total_n, total_t
+
+
+# ------------------------------------------------------------------ precision form (TC vs FP32)
+
+PF_DIMS = (1024, 1024, 512)
+
+
+def precision_form(args, vkt, torch, dev, stream, peaks):
+    """Split FP16 hi/lo tensor-core path vs plain FP32 path on the 1024x1024x512
+    turbulence-like field with normalised N(0,1) k^3 kernels, k = 7 and 9: Gvoxel/s of
+    each, their ratio, the error of each against the FP64 oracle on sampled voxels, and
+    the tensor pipe's executed FLOP rate against the measured dense FP16/BF16 peak."""
+    import oracle
+    import synth
+    field = synth.volume("fourier", synth.F32, PF_DIMS, synth.BASE_SEED + 2)
+    src = torch.from_numpy(field).to(dev)
+    out = torch.empty_like(src)
+    v_src = vkt.StructuredVolume.from_tensor(src)
+    v_out = vkt.StructuredVolume.from_tensor(out)
+    vox = float(np.prod(PF_DIMS))
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, field.size, 20000)
+    xmax = float(np.abs(field).max())
+    res = {"workload": "fourier 1024x1024x512 f32, normalised N(0,1) kernels", "dims": list(PF_DIMS)}
+    for k in (7, 9):
+        w, seed_used = synth.random_kernel(synth.BASE_SEED + 2, k, 1.0, normalise_sum=True)
+        f = vkt.Filter.dense(w)
+        ref = oracle.correlate_points(field, w, idx)
+        scale = oracle.error_scale(w, xmax)
+        entry = {}
+        for path in ("tensor", "direct"):
+            with vkt.policy(stream=stream, path=path):
+                for _ in range(3):
+                    vkt.check(vkt._lib.vktApplyFilterSV(v_out.handle, v_src.handle, f.handle))
+                torch.cuda.synchronize()
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                evs[0].record(stream)
+                for _ in range(args.precision_reps):
+                    vkt.check(vkt._lib.vktApplyFilterSV(v_out.handle, v_src.handle, f.handle))
+                evs[1].record(stream)
+                torch.cuda.synchronize()
+                vkt.synchronize()
+            ms = evs[0].elapsed_time(evs[1]) / args.precision_reps
+            got = out.view(-1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+            err = float(np.max(np.abs(got - ref)) / scale)
+            entry[path] = {"ms": round(ms, 4), "gvoxel_s": round(vox / (ms * 1e-3) / 1e9, 2),
+                           "max_err_normalised": err}
+        # executed tensor FLOPs: per 128 x 16 output voxels and input plane, 2 x-tiles x k
+        # row offsets x 3 split products of a 128 x N x 16 MMA (N = 8 * even(k)); input
+        # planes per output plane = (zchunk + k - 1) / zchunk
+        slots = ((k + 1) // 2) * 2
+        flops_plane = 2 * k * 3 * (128 * 8 * slots * 16 * 2)
+        tc = entry["tensor"]
+        tc_tflops = flops_plane / 2048 * vox / (tc["ms"] * 1e-3) / 1e12
+        alg_tflops = 2 * k ** 3 * vox / (tc["ms"] * 1e-3) / 1e12
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        entry["tc_over_fp32"] = round(entry["direct"]["ms"] / tc["ms"], 3)
+        entry["tensor_roofline"] = {"bound": "tensor", "executed_tflops_lower_bound": round(tc_tflops, 1),
+                                    "algorithmic_tflops": round(alg_tflops, 1),
+                                    "peak": bf16, "unit": "TFLOP/s",
+                                    "frac": round(tc_tflops / bf16, 4),
+                                    "peak_source": "measured bf16_tflops (dense fp16 has the same rate)"}
+        entry["kernel_seed"] = seed_used
+        res[f"k{k}"] = entry
+    return res
 
 
 # ------------------------------------------------------------------ our arm
@@ -287,6 +356,10 @@ def run_ours(args):
                "kind": "oracle",
                "sample": f"{n} random voxels of the 512^3 volume, both filters, FP64 C, {dt:.1f} s"}
 
+    pform = None
+    if not args.no_precision_form:
+        pform = precision_form(args, vkt, torch, dev, stream, peaks)
+
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -297,7 +370,7 @@ def run_ours(args):
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk,
+            "gpu_launches": launches, "clocks": clk, "precision_form": pform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

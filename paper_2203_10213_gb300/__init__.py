@@ -337,3 +337,57 @@ def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
     dst = StructuredVolume.from_tensor(out, *dst_range)
     apply_filter(dst, src, filt, path=path)
     return out
+
+
+# ------------------------------------------------------------------ autograd
+
+def _autograd_function():
+    import torch
+
+    class ApplyFilterFunction(torch.autograd.Function):
+        """y = ApplyFilter(x, w) for float32 volumes x of shape (nz, ny, nx) or (B, nz, ny, nx)
+        and a dense k^3 float32 kernel w; backward calls vktApplyFilterBackwardSV (exact
+        adjoint for dL/dx, FP64-reduced dL/dw)."""
+
+        @staticmethod
+        def forward(ctx, x, w, path="auto"):
+            if x.dtype != torch.float32 or w.dtype != torch.float32:
+                raise TypeError("ApplyFilterFunction takes float32 volumes and weights")
+            xb = x.contiguous().reshape((-1,) + tuple(x.shape[-3:]))
+            filt = Filter.dense(w.detach().float().cpu().numpy())
+            y = torch.empty_like(xb)
+            for b in range(xb.shape[0]):
+                apply_filter(StructuredVolume.from_tensor(y[b]), StructuredVolume.from_tensor(xb[b]),
+                             filt, path=path)
+            ctx.save_for_backward(xb, w)
+            ctx.shape = x.shape
+            return y.reshape(x.shape)
+
+        @staticmethod
+        def backward(ctx, gy):
+            xb, w = ctx.saved_tensors
+            gyb = gy.contiguous().reshape(xb.shape)
+            filt = Filter.dense(w.detach().float().cpu().numpy())
+            need_x, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+            gx = torch.empty_like(xb) if need_x else None
+            gws = torch.empty((xb.shape[0], w.numel()), dtype=torch.float32, device=xb.device) if need_w else None
+            for b in range(xb.shape[0]):
+                apply_filter_backward(StructuredVolume.from_tensor(gx[b]) if need_x else None,
+                                      gws[b] if need_w else None,
+                                      StructuredVolume.from_tensor(gyb[b]),
+                                      StructuredVolume.from_tensor(xb[b]), filt)
+            gw = gws.sum(0).reshape(w.shape) if need_w else None
+            return (gx.reshape(ctx.shape) if need_x else None), gw, None
+
+    return ApplyFilterFunction
+
+
+_APPLY_FN = None
+
+
+def apply_filter_autograd(x, w, path="auto"):
+    """Differentiable ApplyFilter on float32 CUDA tensors (see ApplyFilterFunction)."""
+    global _APPLY_FN
+    if _APPLY_FN is None:
+        _APPLY_FN = _autograd_function()
+    return _APPLY_FN.apply(x, w, path)

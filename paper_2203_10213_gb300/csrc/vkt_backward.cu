@@ -1,0 +1,265 @@
+// vkt_backward.cu -- gradients of the float32 clamped correlation y = C_w x:
+//   dL/dx : exact adjoint, evaluated by the direct kernel in adjoint mode (vkt_direct.cu);
+//   dL/dw[c][b][a] = sum_i gy(i) x(clamp(i + (a-r, b-r, c-r))), evaluated here.
+//
+// Weight gradient: CTA (c, x tile, y tile, z chunk) owns one kernel plane offset c and a
+// 64 x 32 x zchunk brick of output positions i.  It streams the x planes z + c - r (TMA,
+// clamp-to-edge conversion into a float tile, recomputed from HBM instead of stored) and
+// the gy planes z, and accumulates the k^2 sums over (b, a) in registers: k^2 FMAs per
+// voxel per CTA, k^3 over the k CTAs that share a tile.  The CTA reduces its sums (warp
+// shuffles, then shared memory) to one FP32 partial per tap; a second kernel adds the
+// partials of all CTAs in FP64 and writes float32 dL/dw.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "vkt_internal.h"
+#include "vkt_tile.cuh"
+
+namespace vkt {
+namespace {
+
+constexpr int NT = 256;
+constexpr int BX = 16, BY = 16, RX = 4, RY = 2;
+constexpr int TX = BX * RX, TY = BY * RY;
+constexpr int STAGES = 4;
+
+struct WgArgs {
+    const float* x;
+    const float* gy;
+    float* partials;     // [nspatial][k^3]
+    int nx, ny, nz;
+    int tiles_x, tiles_y, zchunk;
+    int use_tma;
+    unsigned* status;
+};
+
+template <int K>
+constexpr size_t wgrad_smem_bytes()
+{
+    using Geo = Brick<K, TX, TY>;
+    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(FMT_F32) +
+           2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +
+           static_cast<size_t>(NT / 32) * K * K * sizeof(float);
+}
+
+template <int K>
+__global__ void __launch_bounds__(NT)
+    k_wgrad(const __grid_constant__ CUtensorMap tmap, const WgArgs p)
+{
+    using Geo = Brick<K, TX, TY>;
+    constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    constexpr int rawb = Geo::raw_bytes(FMT_F32);
+    constexpr uint32_t txb = Geo::raw_tx(FMT_F32);
+    unsigned char* raw = smem + 128;
+    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+    float* red = F + 2 * FH * FP;
+
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int tx = tid % BX, ty = tid / BX;
+    const int c = blockIdx.x % K;
+    const int xt = blockIdx.x / K;
+    const int x0 = xt * TX, y0 = blockIdx.y * TY;
+    const int zc0 = blockIdx.z * p.zchunk;
+    const int zc1 = min(zc0 + p.zchunk, p.nz);
+    const int nplanes = max(zc1 - zc0, 0);
+    constexpr int xa = 4;     // float32 x halo that keeps the TMA box 16-byte aligned
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        if (p.use_tma) prefetch_tensor_map(&tmap);
+    }
+    __syncthreads();
+    int issued = 0;
+    // x plane paired with gy plane z is clamp(z + c - r)
+    if (p.use_tma && tid == 0) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(zc0 + s + c - R, 0, p.nz - 1));
+        }
+    }
+    ConvPlan<Geo, NT> plan;
+    plan.init(FMT_F32, p.nx, p.ny, x0, y0, tid);
+
+    float acc[K][K];
+#pragma unroll
+    for (int b = 0; b < K; ++b)
+#pragma unroll
+        for (int a = 0; a < K; ++a) acc[b][a] = 0.f;
+
+    const int ox = x0 + tx * RX;
+    bool failed = false;
+    for (int it = 0; it < nplanes; ++it) {
+        const int s = it % STAGES;
+        const int z = zc0 + it;
+        const unsigned char* rs = raw + s * rawb;
+        float* Fb = F + (it & 1) * FH * FP;
+        bool ok = true;
+        // gy block of this thread (zero outside the volume so it adds nothing)
+        float g[RY][RX];
+#pragma unroll
+        for (int i = 0; i < RY; ++i) {
+            const int oy = y0 + ty * RY + i;
+            const int64_t row = (static_cast<int64_t>(z) * p.ny + oy) * p.nx;
+#pragma unroll
+            for (int x = 0; x < RX; ++x)
+                g[i][x] = (oy < p.ny && ox + x < p.nx) ? __ldg(p.gy + row + ox + x) : 0.f;
+        }
+        if (p.use_tma) {
+            ok = mbar_wait(&bars[s], (it / STAGES) & 1);
+        } else {
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), p.x, FMT_F32,
+                                    p.nx, p.ny, p.nz, x0, y0, z + c - R, tid);
+            __syncthreads();
+        }
+        if (ok) plan.convert(rs, FMT_F32, Fb, tid);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(zc0 + it + STAGES + c - R, 0, p.nz - 1));
+            ++issued;
+        }
+#pragma unroll
+        for (int j = 0; j < RY + K - 1; ++j) {
+            float win[RX + K - 1];
+            load_row<RX + K - 1, RX>(Fb + (ty * RY + j) * FP + tx * RX, win);
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                const int b = j - i;
+                if (b < 0 || b >= K) continue;
+#pragma unroll
+                for (int a = 0; a < K; ++a)
+#pragma unroll
+                    for (int x = 0; x < RX; ++x) acc[b][a] = fmaf(g[i][x], win[x + a], acc[b][a]);
+            }
+        }
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(p.status, STATUS_TIMEOUT);
+            for (int q = issued - 1; q >= 0 && q >= issued - STAGES; --q)
+                mbar_wait(&bars[q % STAGES], (q / STAGES) & 1);
+        }
+        __syncthreads();
+        return;
+    }
+    // CTA reduction of the K*K sums: warps, then shared memory
+#pragma unroll
+    for (int b = 0; b < K; ++b)
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            float v = acc[b][a];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * K * K + b * K + a] = v;
+        }
+    __syncthreads();
+    const int spatial = (blockIdx.z * p.tiles_y + blockIdx.y) * p.tiles_x + xt;
+    for (int t = tid; t < K * K; t += NT) {
+        float v = 0.f;
+        for (int w = 0; w < NT / 32; ++w) v += red[w * K * K + t];
+        p.partials[static_cast<int64_t>(spatial) * K * K * K + c * K * K + t] = v;
+    }
+}
+
+// dL/dw[d] = sum over CTAs of partials[cta][d], in FP64; one warp per tap
+__global__ void k_wgrad_reduce(const float* partials, int nspatial, int kkk, float* gw)
+{
+    const int d = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (d >= kkk) return;
+    double s = 0.0;
+    for (int i = lane; i < nspatial; i += 32) s += static_cast<double>(partials[static_cast<int64_t>(i) * kkk + d]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) gw[d] = static_cast<float>(s);
+}
+
+struct Geometry {
+    int tiles_x, tiles_y, chunks, zchunk;
+};
+
+Geometry geometry(int nx, int ny, int nz, int k)
+{
+    Geometry g;
+    g.tiles_x = (nx + TX - 1) / TX;
+    g.tiles_y = (ny + TY - 1) / TY;
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long target = static_cast<long>(sms) * 8;
+    const long xyc = static_cast<long>(g.tiles_x) * g.tiles_y * k;
+    g.chunks = static_cast<int>(std::max<long>(1, std::min<long>((target + xyc - 1) / xyc, std::max(1, nz / 8))));
+    g.zchunk = (nz + g.chunks - 1) / g.chunks;
+    g.chunks = (nz + g.zchunk - 1) / g.zchunk;
+    return g;
+}
+
+template <int K>
+vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, float* partials,
+                   size_t cap, float* gw, const Ctx& ctx)
+{
+    using Geo = Brick<K, TX, TY>;
+    const Geometry g = geometry(nx, ny, nz, K);
+    const size_t nspatial = static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks;
+    if (nspatial * K * K * K > cap) return VKT_ERROR_INVALID_VALUE;
+    WgArgs a;
+    a.x = x;
+    a.gy = gy;
+    a.partials = partials;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.tiles_x = g.tiles_x;
+    a.tiles_y = g.tiles_y;
+    a.zchunk = g.zchunk;
+    a.status = ctx.status;
+    alignas(64) CUtensorMap map;
+    a.use_tma = encode_tensor_map_3d(&map, FMT_F32, x, nx, ny, nz, Geo::raw_w(FMT_F32), Geo::FH, 1) ? 1 : 0;
+    if (!a.use_tma) memset(&map, 0, sizeof(map));
+    const size_t smem = wgrad_smem_bytes<K>();
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return from_cuda(e);
+    if (ctx.debug)
+        fprintf(stderr, "[vkt] wgrad k=%d grid=(%d,%d,%d) zchunk=%d tma=%d\n", K, g.tiles_x * K,
+                g.tiles_y, g.chunks, g.zchunk, a.use_tma);
+    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, ctx.stream>>>(map, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return from_cuda(e);
+    const int kkk = K * K * K;
+    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, ctx.stream>>>(partials, static_cast<int>(nspatial), kkk, gw);
+    count_launches(2);
+    return from_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k)
+{
+    const Geometry g = geometry(nx, ny, nz, k);
+    return static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks * k * k * k;
+}
+
+vktError launch_weight_grad(const float* x, const float* gy, int nx, int ny, int nz, int k,
+                            float* partials, size_t cap, float* gw, const Ctx& ctx)
+{
+    switch (k) {
+    case 1: return launch_wg<1>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    case 3: return launch_wg<3>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    case 5: return launch_wg<5>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    case 7: return launch_wg<7>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    case 9: return launch_wg<9>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    default: return VKT_ERROR_UNSUPPORTED;
+    }
+}
+
+}  // namespace vkt

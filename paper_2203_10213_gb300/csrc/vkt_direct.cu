@@ -9,6 +9,15 @@
 //   K <= 3 : the K accumulator planes rotate by unrolling the plane loop K times;
 //   K >= 5 : they rotate by shifting once per plane (less code for the same arithmetic).
 // Weights travel as kernel parameters and enter the FMAs as constant-bank operands.
+//
+// Adjoint mode (ADJ): the same machinery evaluates dL/dx of the clamped correlation.  With
+// the extension E (x_ext(j) = x(clamp(j)) on the domain padded by r), the forward filter is
+// a plain correlation of x_ext, so its adjoint is E^T applied to the zero-padded correlation
+// of gy with the flipped kernel, Z(j') = sum_d w[-d] gy0(j' + d) for j' in [-r, n+r)^3.
+// E^T folds Z onto the volume: gx(j) = sum of Z(j') over the j' whose clamp is j.  The
+// kernel computes Z brick by brick (TMA zero-fills positions outside gy), stores Z
+// directly where j' is strictly inside the volume (exactly one contribution) and
+// atomically adds it to the face voxel clamp(j') everywhere else.
 #include <algorithm>
 #include <cstdio>
 
@@ -31,6 +40,8 @@ struct DirectArgs {
     const void* src;
     void* dst;
     int nx, ny, nz;
+    int ox0, oy0, oz0;     // origin of the output domain (0, or the padded domain's corner)
+    int ex, ey, ez;        // extent of the output domain
     int sfmt, dfmt;
     int zchunk;
     int use_tma;
@@ -55,7 +66,28 @@ __host__ __device__ constexpr size_t direct_smem_bytes(int sfmt)
            2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
 }
 
-template <int K>
+// Adjoint store of one row of Z values at padded-domain positions (oz, oy, ox + x).
+template <int RX>
+__device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, int nz, int R, int oz,
+                                                  int oy, int ox, const float (&z)[RX])
+{
+    if (oy < -R || oy >= ny + R || oz < -R || oz >= nz + R) return;
+    const int cy = clampi(oy, 0, ny - 1), cz = clampi(oz, 0, nz - 1);
+    const bool inner_yz = oy > 0 && oy < ny - 1 && oz > 0 && oz < nz - 1;
+    const int64_t rowbase = (static_cast<int64_t>(cz) * ny + cy) * nx;
+#pragma unroll
+    for (int x = 0; x < RX; ++x) {
+        const int xx = ox + x;
+        if (xx < -R || xx >= nx + R) continue;
+        const int cx = clampi(xx, 0, nx - 1);
+        if (inner_yz && xx > 0 && xx < nx - 1)
+            dst[rowbase + cx] = z[x];
+        else
+            atomicAdd(dst + rowbase + cx, z[x]);
+    }
+}
+
+template <int K, bool ADJ>
 __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
@@ -73,9 +105,9 @@ __global__ void __launch_bounds__(NT)
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int x0 = blockIdx.x * Cfg::TX, y0 = blockIdx.y * Cfg::TY;
-    const int zc0 = blockIdx.z * p.zchunk;
-    const int zc1 = min(zc0 + p.zchunk, p.nz);
+    const int x0 = p.ox0 + blockIdx.x * Cfg::TX, y0 = p.oy0 + blockIdx.y * Cfg::TY;
+    const int zc0 = p.oz0 + blockIdx.z * p.zchunk;
+    const int zc1 = min(zc0 + p.zchunk, p.oz0 + p.ez);
     if (zc0 >= zc1) return;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
@@ -92,11 +124,11 @@ __global__ void __launch_bounds__(NT)
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(pfirst + s, 0, p.nz - 1));
+                        ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1));
         }
     }
 
-    ConvPlan<Geo, NT> plan;
+    ConvPlan<Geo, NT, !ADJ> plan;
     plan.init(p.sfmt, p.nx, p.ny, x0, y0, tid);
 
     float acc[K][RY][RX];
@@ -120,8 +152,8 @@ __global__ void __launch_bounds__(NT)
         if (p.use_tma) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
-            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), p.src, p.sfmt, p.nx, p.ny,
-                                    x0, y0, clampi(pfirst + it, 0, p.nz - 1), tid);
+            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, p.sfmt, p.nx,
+                                          p.ny, p.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
         if (ok) plan.convert(rs, p.sfmt, Fb, tid);
@@ -132,7 +164,7 @@ __global__ void __launch_bounds__(NT)
         if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(pfirst + it + STAGES, 0, p.nz - 1));
+                        ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1));
             ++issued;
         }
         // multiply the plane into the accumulators
@@ -162,7 +194,10 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const int oy = y0 + ty * RY + i;
-                if (oy < p.ny && nvalid > 0) {
+                if (ADJ) {
+                    store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
+                                          ox, acc[sl0][i]);
+                } else if (oy < p.ny && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
                     store_row<RX>(p.dst, p.dfmt, idx, nvalid, acc[sl0][i], p.a0, p.a1, p.qmax);
                 }
@@ -212,11 +247,12 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-template <int K>
+template <int K, bool ADJ>
 vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
 {
     using Cfg = DirectCfg<K>;
     using Geo = typename Cfg::Geo;
+    constexpr int R = Geo::R;
     DirectArgs a;
     a.src = job.src;
     a.dst = job.dst;
@@ -229,11 +265,27 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     a.a1 = job.a1;
     a.qmax = job.qmax;
     a.status = ctx.status;
+    if (ADJ) {
+        // padded output domain [-r, n+r) per axis; x starts 16 bytes left of the domain
+        // so that every tile's TMA box starts on a 16-byte boundary
+        a.ox0 = -fmt_xalign(job.sfmt);
+        a.oy0 = -R;
+        a.oz0 = -R;
+        a.ex = job.nx + R - a.ox0;
+        a.ey = job.ny + 2 * R;
+        a.ez = job.nz + 2 * R;
+    } else {
+        a.ox0 = a.oy0 = a.oz0 = 0;
+        a.ex = job.nx;
+        a.ey = job.ny;
+        a.ez = job.nz;
+    }
     DenseW<K> W;
-    for (int i = 0; i < K * K * K; ++i) W.w[i] = w[i];
+    const int kk = K * K * K;
+    for (int i = 0; i < kk; ++i) W.w[i] = ADJ ? w[kk - 1 - i] : w[i];   // adjoint: w[-d]
 
-    const int gx = (job.nx + Cfg::TX - 1) / Cfg::TX;
-    const int gy = (job.ny + Cfg::TY - 1) / Cfg::TY;
+    const int gx = (a.ex + Cfg::TX - 1) / Cfg::TX;
+    const int gy = (a.ey + Cfg::TY - 1) / Cfg::TY;
     int sms = 152;
     {
         int dev = 0;
@@ -242,10 +294,10 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     }
     const long target = static_cast<long>(sms) * 8;   // ~2 waves of 4 CTAs per SM
     const long xy = static_cast<long>(gx) * gy;
-    int chunks = static_cast<int>(std::min<long>((target + xy - 1) / xy, std::max(1, job.nz / 8)));
+    int chunks = static_cast<int>(std::min<long>((target + xy - 1) / xy, std::max(1, a.ez / 8)));
     chunks = std::max(chunks, 1);
-    a.zchunk = (job.nz + chunks - 1) / chunks;
-    const int gz = (job.nz + a.zchunk - 1) / a.zchunk;
+    a.zchunk = (a.ez + chunks - 1) / chunks;
+    const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
 
     alignas(64) CUtensorMap map;
     const int rawx = Geo::raw_w(job.sfmt);
@@ -256,13 +308,14 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     if (!a.use_tma) memset(&map, 0, sizeof(map));
 
     const size_t smem = direct_smem_bytes<K>(job.sfmt);
-    cudaError_t e = cudaFuncSetAttribute(k_direct<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_direct<K, ADJ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
     if (ctx.debug)
-        fprintf(stderr, "[vkt] direct k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n", K, gx,
-                gy, gz, a.zchunk, smem, a.use_tma);
-    k_direct<K><<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
+        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
+                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma);
+    k_direct<K, ADJ><<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
     count_launches(1);
     return from_cuda(cudaGetLastError());
 }
@@ -272,11 +325,23 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
 vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx)
 {
     switch (k) {
-    case 1: return launch_k<1>(job, w, ctx);
-    case 3: return launch_k<3>(job, w, ctx);
-    case 5: return launch_k<5>(job, w, ctx);
-    case 7: return launch_k<7>(job, w, ctx);
-    case 9: return launch_k<9>(job, w, ctx);
+    case 1: return launch_k<1, false>(job, w, ctx);
+    case 3: return launch_k<3, false>(job, w, ctx);
+    case 5: return launch_k<5, false>(job, w, ctx);
+    case 7: return launch_k<7, false>(job, w, ctx);
+    case 9: return launch_k<9, false>(job, w, ctx);
+    default: return VKT_ERROR_UNSUPPORTED;
+    }
+}
+
+vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx)
+{
+    switch (k) {
+    case 1: return launch_k<1, true>(job, w, ctx);
+    case 3: return launch_k<3, true>(job, w, ctx);
+    case 5: return launch_k<5, true>(job, w, ctx);
+    case 7: return launch_k<7, true>(job, w, ctx);
+    case 9: return launch_k<9, true>(job, w, ctx);
     default: return VKT_ERROR_UNSUPPORTED;
     }
 }

@@ -48,6 +48,14 @@ struct Ctx {
 
 // Kernel launchers (each returns VKT_NO_ERROR or a launch error).
 vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx);
+// dL/dsrc of the clamped correlation (float32 gy in job.src, gx in job.dst; gx must be
+// zeroed first: face voxels are accumulated atomically).
+vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx);
+// dL/dw: per-CTA FP32 partial sums into `partials` (capacity `cap` floats), then an FP64
+// reduction into gw (k^3 floats).  `partials` is caller-provided scratch.
+vktError launch_weight_grad(const float* x, const float* gy, int nx, int ny, int nz, int k,
+                            float* partials, size_t cap, float* gw, const Ctx& ctx);
+size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k);
 vktError launch_separable(const Job& job, const float* gx, const float* gy, const float* gz,
                           int k, const Ctx& ctx);
 

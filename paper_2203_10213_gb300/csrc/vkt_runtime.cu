@@ -621,4 +621,59 @@ vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktF
     return err;
 }
 
+vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeights,
+                                  vktStructuredVolume gradDst, vktStructuredVolume src,
+                                  vktFilter filter)
+{
+    if (!valid(gradDst) || !valid(src) || !valid(filter)) return VKT_ERROR_INVALID_HANDLE;
+    if (gradSrc && !valid(gradSrc)) return VKT_ERROR_INVALID_HANDLE;
+    if (src->format != vktDataFormatFloat32 || gradDst->format != vktDataFormatFloat32 ||
+        (gradSrc && gradSrc->format != vktDataFormatFloat32))
+        return VKT_ERROR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a) {
+        if (gradDst->dims[a] != src->dims[a]) return VKT_ERROR_DIMS_MISMATCH;
+        if (gradSrc && gradSrc->dims[a] != src->dims[a]) return VKT_ERROR_DIMS_MISMATCH;
+    }
+    if (gradSrc && (overlaps(gradSrc, gradDst) || overlaps(gradSrc, src)))
+        return VKT_ERROR_INVALID_VALUE;
+    if (reinterpret_cast<uintptr_t>(gradWeights) % 4 != 0) return VKT_ERROR_INVALID_VALUE;
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+    const int k = filter->k;
+    const int nx = src->dims[0], ny = src->dims[1], nz = src->dims[2];
+    if (gradSrc) {
+        // face voxels of dL/dsrc are accumulated atomically: start from zero
+        cudaError_t e = cudaMemsetAsync(gradSrc->data, 0, volume_bytes(gradSrc), ctx.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        Job job;
+        job.src = gradDst->data;
+        job.dst = gradSrc->data;
+        job.nx = nx;
+        job.ny = ny;
+        job.nz = nz;
+        job.sfmt = vktDataFormatFloat32;
+        job.dfmt = vktDataFormatFloat32;
+        job.a0 = 0.f;
+        job.a1 = 1.f;
+        job.qmax = 0.f;
+        err = launch_adjoint(job, filter->w, k, ctx);
+        if (err != VKT_NO_ERROR) return err;
+    }
+    if (gradWeights) {
+        // per-CTA partial sums live in stream-ordered scratch for the duration of the call
+        const size_t cap = weight_grad_scratch_floats(nx, ny, nz, k);
+        float* partials = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&partials), cap * sizeof(float),
+                                        ctx.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        err = launch_weight_grad(static_cast<const float*>(src->data),
+                                 static_cast<const float*>(gradDst->data), nx, ny, nz, k, partials,
+                                 cap, gradWeights, ctx);
+        e = cudaFreeAsync(partials, ctx.stream);
+        if (err == VKT_NO_ERROR && e != cudaSuccess) err = from_cuda(e);
+    }
+    return err;
+}
+
 }  // extern "C"

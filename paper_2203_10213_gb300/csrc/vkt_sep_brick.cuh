@@ -1,0 +1,243 @@
+// vkt_sep_brick.cuh -- one brick of the fused separable filter (three 1-D passes), shared by
+// the single-volume kernel (vkt_separable.cu) and the batched persistent kernel
+// (vkt_batch.cu).
+//
+// The clamp-to-edge correlation with w[c][b][a] = gz[c] gy[b] gx[a] factorises per axis,
+// so it equals an x pass, then a y pass, then a z pass, each clamped at its own faces.  A
+// brick is a TX x TY column of outputs over a chunk of z.  Per input plane: TMA brings the
+// raw tile (with halo) into a ring of stages, it is converted to float with clamping, the
+// x pass writes (TY+2r) x TX partial sums to shared memory, the y pass reduces them to the
+// thread's RY x RX block in registers, and the z pass adds gz[c] times that block into the
+// K output planes the input plane touches (K x RY x RX register accumulators); one output
+// plane completes per input plane.  HBM traffic: the source once, the destination once.
+#pragma once
+
+#include "vkt_internal.h"
+#include "vkt_tile.cuh"
+
+namespace vkt {
+namespace sep {
+
+constexpr int NT = 256;
+constexpr int BX = 16, BY = 16;
+constexpr int RX = 4, RY = 2;
+constexpr int TX = BX * RX, TY = BY * RY;
+constexpr int STAGES = 4;
+
+// Everything a brick needs about its volume (the batched kernel reads these from a table).
+struct Job {
+    const void* src;
+    void* dst;
+    int nx, ny, nz;
+    int sfmt, dfmt;
+    int zchunk;
+    int use_tma;
+    int k;
+    int tiles_x, tiles_y, chunks;
+    float a0, a1, qmax;
+    float g[3][VKT_MAX_FILTER_SIZE];    // x, y, z vectors
+};
+
+template <int K>
+struct W {
+    float gx[K], gy[K], gz[K];
+};
+
+template <int K>
+__host__ __device__ constexpr size_t smem_bytes(int sfmt)
+{
+    using Geo = Brick<K, TX, TY>;
+    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+           static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +      // float tile
+           static_cast<size_t>(Geo::FH) * TX * sizeof(float);            // x-pass output
+}
+
+// Initialises the stage barriers (thread 0; the caller synchronises afterwards).
+__device__ __forceinline__ void init_barriers(unsigned char* smem)
+{
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+}
+
+// Runs brick (bx, by, bz) of job J.  `gplane` counts the planes this CTA has pipelined so
+// far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring carries on
+// across bricks.  Returns false if a bounded wait timed out (after recording it and
+// draining the loads in flight).
+template <int K, class Wt>
+__device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
+                                      int by, int bz, unsigned char* smem, uint32_t& gplane,
+                                      unsigned* status)
+{
+    using Geo = Brick<K, TX, TY>;
+    constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
+    constexpr int XGROUPS = TX / 4;
+    constexpr int XITEMS = FH * XGROUPS;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    const int rawb = Geo::raw_bytes(J.sfmt);
+    const uint32_t txb = Geo::raw_tx(J.sfmt);
+    unsigned char* raw = smem + 128;
+    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+    float* T1 = F + FH * FP;
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int x0 = bx * TX, y0 = by * TY;
+    const int zc0 = bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, J.nz);
+    if (zc0 >= zc1) return true;
+    const int pfirst = zc0 - R;
+    const int nplanes = zc1 - zc0 + 2 * R;
+    const int xa = fmt_xalign(J.sfmt);
+    const uint32_t g0 = gplane;
+
+    int issued = 0;
+    if (J.use_tma && tid == 0) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+            const uint32_t q = g0 + s;
+            mbar_arrive_expect_tx(&bars[q % STAGES], txb);
+            tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
+                        clampi(pfirst + s, 0, J.nz - 1));
+        }
+    }
+
+    ConvPlan<Geo, NT> plan;
+    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid);
+
+    float acc[K][RY][RX];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int i = 0; i < RY; ++i)
+#pragma unroll
+            for (int x = 0; x < RX; ++x) acc[s][i][x] = 0.f;
+
+    const int ox = x0 + tx * RX;
+    const int nvalid = J.nx - ox;
+    bool failed = false;
+
+    auto plane = [&](const int it, const int u) {
+        const uint32_t q = g0 + it;
+        const int s = q % STAGES;
+        const unsigned char* rs = raw + s * rawb;
+        bool ok = true;
+        if (J.use_tma) {
+            ok = mbar_wait(&bars[s], (q / STAGES) & 1);
+        } else {
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, J.sfmt, J.nx, J.ny,
+                                    J.nz, x0, y0, pfirst + it, tid);
+            __syncthreads();
+        }
+        if (ok) plan.convert(rs, J.sfmt, F, tid);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            return;
+        }
+        if (J.use_tma && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(pfirst + it + STAGES, 0, J.nz - 1));
+            ++issued;
+        }
+        // x pass: T1[row][x] = sum_a gx[a] F[row][x + a], 4 outputs per item
+#pragma unroll
+        for (int n = 0; n < (XITEMS + NT - 1) / NT; ++n) {
+            const int item = tid + n * NT;
+            if (item < XITEMS) {
+                const int row = item / XGROUPS, g = item - row * XGROUPS;
+                float win[4 + K - 1];
+                load_row<4 + K - 1, 4>(F + row * FP + 4 * g, win);
+                float4 o;
+                float* op = &o.x;
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int a = 0; a < K; ++a) t = fmaf(G.gx[a], win[x + a], t);
+                    op[x] = t;
+                }
+                *reinterpret_cast<float4*>(T1 + row * TX + 4 * g) = o;
+            }
+        }
+        __syncthreads();
+        // y pass into registers, then the z pass into the K rotating accumulator planes
+        float t2[RY][RX];
+#pragma unroll
+        for (int i = 0; i < RY; ++i)
+#pragma unroll
+            for (int x = 0; x < RX; ++x) t2[i][x] = 0.f;
+#pragma unroll
+        for (int j = 0; j < RY + K - 1; ++j) {
+            float v[RX];
+            load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                const int b = j - i;
+                if (b < 0 || b >= K) continue;
+#pragma unroll
+                for (int x = 0; x < RX; ++x) t2[i][x] = fmaf(G.gy[b], v[x], t2[i][x]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const int sl = ((u - c + R) % K + K) % K;
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int x = 0; x < RX; ++x) acc[sl][i][x] = fmaf(G.gz[c], t2[i][x], acc[sl][i][x]);
+        }
+        const int sl0 = ((u - R) % K + K) % K;
+        if (it >= 2 * R) {
+            const int oz = pfirst + it - R;
+#pragma unroll
+            for (int i = 0; i < RY; ++i) {
+                const int oy = y0 + ty * RY + i;
+                if (oy < J.ny && nvalid > 0) {
+                    const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
+                    store_row<RX>(J.dst, J.dfmt, idx, nvalid, acc[sl0][i], J.a0, J.a1, J.qmax);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RY; ++i)
+#pragma unroll
+            for (int x = 0; x < RX; ++x) acc[sl0][i][x] = 0.f;
+    };
+
+    for (int g = 0; g * K < nplanes && !failed; ++g) {
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int it = g * K + u;
+            if (it >= nplanes || failed) break;
+            plane(it, u);
+        }
+    }
+    gplane = g0 + nplanes;
+
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
+                mbar_wait(&bars[(g0 + it) % STAGES], ((g0 + it) / STAGES) & 1);
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// z chunking that gives about 8 CTAs per SM in total over the bricks of one volume
+inline int choose_zchunk(int nx, int ny, int nz, int sms)
+{
+    const long tiles = static_cast<long>((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+    const long target = static_cast<long>(sms) * 8;
+    long chunks = (target + tiles - 1) / tiles;
+    chunks = chunks < 1 ? 1 : chunks;
+    const long cap = nz / 8 < 1 ? 1 : nz / 8;
+    chunks = chunks > cap ? cap : chunks;
+    return static_cast<int>((nz + chunks - 1) / chunks);
+}
+
+}  // namespace sep
+}  // namespace vkt

@@ -126,35 +126,45 @@ __device__ __forceinline__ float load_global(const void* src, int fmt, int64_t i
     return static_cast<float>(__ldg(reinterpret_cast<const unsigned char*>(src) + idx));
 }
 
-// Fills the raw tile of plane z with plain loads at clamped coordinates (the path for
-// volumes whose rows cannot be described by a tensor map).  Positions outside the
-// volume receive the clamped neighbour, which the conversion never reads anyway.
-template <typename Geo, int NT>
+// Fills the raw tile of plane z with plain loads (the path for volumes whose rows cannot
+// be described by a tensor map).  CLAMP: positions outside the volume receive the clamped
+// neighbour (the conversion never reads them anyway); otherwise they receive zero, the
+// zero extension the adjoint needs (and what a TMA load writes there).
+template <typename Geo, int NT, bool CLAMP = true>
 __device__ __forceinline__ void fill_raw_plain(unsigned char* raw, const void* src, int fmt,
-                                               int nx, int ny, int x0, int y0, int z, int tid)
+                                               int nx, int ny, int nz, int x0, int y0, int z,
+                                               int tid)
 {
     const int xa = fmt_xalign(fmt);
     const int rw = Geo::raw_w(fmt);
     const int n = rw * Geo::FH;
-    const int64_t plane = static_cast<int64_t>(z) * nx * ny;
+    const bool zin = z >= 0 && z < nz;
+    const int zc = clampi(z, 0, nz - 1);
+    const int64_t plane = static_cast<int64_t>(zc) * nx * ny;
     for (int e = tid; e < n; e += NT) {
         const int row = e / rw, col = e - row * rw;
-        const int gy = clampi(y0 - Geo::R + row, 0, ny - 1);
-        const int gx = clampi(x0 - xa + col, 0, nx - 1);
+        const int yy = y0 - Geo::R + row, xx = x0 - xa + col;
+        const bool in = zin && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
+        const int gy = clampi(yy, 0, ny - 1);
+        const int gx = clampi(xx, 0, nx - 1);
         const int64_t gi = plane + static_cast<int64_t>(gy) * nx + gx;
-        if (fmt == FMT_F32)
-            reinterpret_cast<float*>(raw)[e] = __ldg(reinterpret_cast<const float*>(src) + gi);
-        else if (fmt == FMT_U16)
-            reinterpret_cast<uint16_t*>(raw)[e] = __ldg(reinterpret_cast<const uint16_t*>(src) + gi);
-        else
-            raw[e] = __ldg(reinterpret_cast<const unsigned char*>(src) + gi);
+        if (fmt == FMT_F32) {
+            const float v = __ldg(reinterpret_cast<const float*>(src) + gi);
+            reinterpret_cast<float*>(raw)[e] = (CLAMP || in) ? v : 0.f;
+        } else if (fmt == FMT_U16) {
+            const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(src) + gi);
+            reinterpret_cast<uint16_t*>(raw)[e] = (CLAMP || in) ? v : 0;
+        } else {
+            const unsigned char v = __ldg(reinterpret_cast<const unsigned char*>(src) + gi);
+            raw[e] = (CLAMP || in) ? v : 0;
+        }
     }
 }
 
 // Per-thread precomputed raw-tile offsets of the float-tile groups this thread converts.
 // Group gi covers float-tile row gi / FGROUPS, columns 4*(gi % FGROUPS) .. +3; each of
 // its 4 elements reads the raw tile at the clamped voxel position.
-template <typename Geo, int NT>
+template <typename Geo, int NT, bool CLAMP = true>
 struct ConvPlan {
     static constexpr int NG = (Geo::FH * Geo::FGROUPS + NT - 1) / NT;
     int off[NG][4];
@@ -168,13 +178,15 @@ struct ConvPlan {
             const int gi = tid + n * NT;
             const int row = gi / Geo::FGROUPS;
             const int g = gi - row * Geo::FGROUPS;
-            const int gy = clampi(y0 - Geo::R + row, 0, ny - 1);
+            // CLAMP: the clamped voxel; otherwise the position itself (the raw tile holds
+            // zeros outside the volume there)
+            const int gy = CLAMP ? clampi(y0 - Geo::R + row, 0, ny - 1) : y0 - Geo::R + row;
             const int rrow = gy - (y0 - Geo::R);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 // padding columns past the halo repeat the last halo column
                 const int j = min(4 * g + e, Geo::FW - 1);
-                const int gx = clampi(x0 - Geo::R + j, 0, nx - 1);
+                const int gx = CLAMP ? clampi(x0 - Geo::R + j, 0, nx - 1) : x0 - Geo::R + j;
                 off[n][e] = rrow * rw + (gx - (x0 - xa));
             }
         }

@@ -232,6 +232,39 @@ VKT_API vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gr
                                   vktStructuredVolume gradDst, vktStructuredVolume src,
                                   vktFilter filter);
 
+/* ------------------------------------------------------------------ allocation-free variant */
+
+/*
+ * The paper has no counterpart to this call; it is a service for callers that cannot
+ * allocate device memory.  vktApplyFilterBackwardSV takes its per-CTA partial sums from
+ * stream-ordered scratch (cudaMallocAsync), and the library's first call on a device also
+ * allocates a small status word.  Some hosts cannot allow that: a process whose device
+ * memory is reserved up front by its own allocator (a framework's caching allocator or a
+ * fixed memory budget), or latency-critical code that must avoid the allocator's locks and
+ * its implicit synchronisation.  This entry point computes the same weight gradient but
+ * allocates nothing: its scratch is a fixed array in the library's own device memory,
+ * VKT_NOALLOC_SCRATCH_FLOATS floats (1 MiB), which every GPU that loads the library holds
+ * until the process exits.
+ *
+ *   gradWeights  device float*, k^3 entries: dL/dw[c][b][a] = sum_i gradDst[i] *
+ *                src[clamp(i + (a-r, b-r, c-r))], reduced in FP64 (as vktApplyFilterBackwardSV)
+ *   gradDst, src float32 volumes with equal dims
+ *
+ * The first call on a device looks up the scratch array's device address (once per device,
+ * with that device current); make that first call before any stream capture.  Work goes to
+ * the calling thread's policy stream.  Every call on a device shares the one scratch array
+ * and it keeps the previous call's contents (each call overwrites all the entries it reads),
+ * so calls whose work overlaps on the GPU race: issue them on one stream, or synchronise in
+ * between.  Returns VKT_ERROR_INVALID_VALUE when the volume needs more partial sums than the
+ * scratch holds (about 64 x 32 voxel tiles times k^3 of them, with the z chunking reduced to
+ * fit), VKT_ERROR_UNSUPPORTED for non-float32 volumes, and the errors of
+ * vktApplyFilterBackwardSV otherwise.  A bounded device wait that times out is not reported
+ * by this call; gradWeights is then undefined.
+ */
+#define VKT_NOALLOC_SCRATCH_FLOATS (1u << 18)
+VKT_API vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStructuredVolume gradDst,
+                                                   vktStructuredVolume src, vktFilter filter);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,6 +59,7 @@ SIGNATURES = {
     "vktApplyFilterSV": [p, p, p],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
+    "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],
 }
 
 

@@ -263,3 +263,128 @@ vktError launch_weight_grad(const float* x, const float* gy, int nx, int ny, int
 }
 
 }  // namespace vkt
+
+// ------------------------------------------------------------------ allocation-free variant
+//
+// For callers that cannot let the library allocate device memory (see vkt.h): the per-CTA
+// partial sums of the weight gradient live in this fixed array instead of stream-ordered
+// scratch, and the kernels' status word lives next to it.  Host code must not pass these
+// names to a kernel (on the host they name a stand-in, not a device address): their device
+// addresses are looked up once per device with cudaGetSymbolAddress.
+
+#include <mutex>
+
+static __device__ __align__(256) float g_noalloc_partials[VKT_NOALLOC_SCRATCH_FLOATS];
+static __device__ __align__(256) unsigned g_noalloc_status[4];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+unsigned* g_noalloc_status_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// device addresses of the scratch array and status word on the current device
+vktError noalloc_scratch(float** partials, unsigned** status)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return vkt::from_cuda(e);
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return VKT_ERROR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        void* q = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess) return vkt::from_cuda(e);
+        e = cudaGetSymbolAddress(&q, g_noalloc_status);
+        if (e != cudaSuccess) return vkt::from_cuda(e);
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+        g_noalloc_status_ptr[dev] = static_cast<unsigned*>(q);
+    }
+    *partials = g_noalloc_ptr[dev];
+    *status = g_noalloc_status_ptr[dev];
+    return VKT_NO_ERROR;
+}
+
+// the weight-gradient kernels with a z chunking small enough for the fixed scratch
+template <int K>
+vktError launch_wg_noalloc(const float* x, const float* gy, int nx, int ny, int nz,
+                           float* partials, unsigned* status, float* gw, cudaStream_t stream)
+{
+    using namespace vkt;
+    using Geo = Brick<K, TX, TY>;
+    Geometry g = geometry(nx, ny, nz, K);
+    const size_t per_chunk = static_cast<size_t>(g.tiles_x) * g.tiles_y * K * K * K;
+    if (per_chunk > VKT_NOALLOC_SCRATCH_FLOATS) return VKT_ERROR_INVALID_VALUE;
+    const int max_chunks = static_cast<int>(VKT_NOALLOC_SCRATCH_FLOATS / per_chunk);
+    if (g.chunks > max_chunks) {
+        g.zchunk = (nz + max_chunks - 1) / max_chunks;
+        g.chunks = (nz + g.zchunk - 1) / g.zchunk;
+    }
+    const int nspatial = g.tiles_x * g.tiles_y * g.chunks;
+    WgArgs a;
+    a.x = x;
+    a.gy = gy;
+    a.partials = partials;
+    a.nx = nx;
+    a.ny = ny;
+    a.nz = nz;
+    a.tiles_x = g.tiles_x;
+    a.tiles_y = g.tiles_y;
+    a.zchunk = g.zchunk;
+    a.status = status;
+    alignas(64) CUtensorMap map;
+    a.use_tma = encode_tensor_map_3d(&map, FMT_F32, x, nx, ny, nz, Geo::raw_w(FMT_F32), Geo::FH, 1) ? 1 : 0;
+    if (!a.use_tma) memset(&map, 0, sizeof(map));
+    const size_t smem = wgrad_smem_bytes<K>();
+    cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return from_cuda(e);
+    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, stream>>>(map, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return from_cuda(e);
+    const int kkk = K * K * K;
+    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, nspatial, kkk, gw);
+    count_launches(2);
+    return from_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStructuredVolume gradDst,
+                                                      vktStructuredVolume src, vktFilter filter)
+{
+    if (!gradDst || gradDst->magic != VKT_VOLUME_MAGIC || !src || src->magic != VKT_VOLUME_MAGIC ||
+        !filter || filter->magic != VKT_FILTER_MAGIC)
+        return VKT_ERROR_INVALID_HANDLE;
+    if (!gradWeights || reinterpret_cast<uintptr_t>(gradWeights) % 4 != 0) return VKT_ERROR_INVALID_VALUE;
+    if (src->format != vktDataFormatFloat32 || gradDst->format != vktDataFormatFloat32)
+        return VKT_ERROR_UNSUPPORTED;
+    for (int a = 0; a < 3; ++a)
+        if (gradDst->dims[a] != src->dims[a]) return VKT_ERROR_DIMS_MISMATCH;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return VKT_ERROR_NO_DEVICE;
+    }
+    float* partials = nullptr;
+    unsigned* status = nullptr;
+    vktError err = noalloc_scratch(&partials, &status);
+    if (err != VKT_NO_ERROR) return err;
+    vktExecutionPolicy pol;
+    vktGetThreadExecutionPolicy(&pol);
+    cudaStream_t stream = static_cast<cudaStream_t>(pol.stream);
+    const float* x = static_cast<const float*>(src->data);
+    const float* gy = static_cast<const float*>(gradDst->data);
+    const int nx = src->dims[0], ny = src->dims[1], nz = src->dims[2];
+    switch (filter->k) {
+    case 1: return launch_wg_noalloc<1>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    case 3: return launch_wg_noalloc<3>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    case 5: return launch_wg_noalloc<5>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    case 7: return launch_wg_noalloc<7>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    case 9: return launch_wg_noalloc<9>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    default: return VKT_ERROR_UNSUPPORTED;
+    }
+}
+

@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the tensor-core vs FP32 comparison on the 1024x1024x512 field")
     ap.add_argument("--precision-reps", type=int, default=10)
+    ap.add_argument("--no-batching-form", action="store_true",
+                    help="skip the 256-volume graph batch vs separate launches comparison")
     return ap.parse_args()
 
 
@@ -212,6 +214,75 @@ def precision_form(args, vkt, torch, dev, stream, peaks):
     return res
 
 
+# ------------------------------------------------------------------ batching form
+
+def batching_form(args, vkt, torch, dev, stream):
+    """256 volumes (dims log-uniform in 16..256 per axis, u8/u16/f32, Gaussian k in {3,5,7},
+    sigma = k/3, dst = src format) in one graph-captured persistent launch, against the
+    same 256 filters issued as separate launches (back to back on one stream, and the sum
+    of individually timed launches)."""
+    import synth
+    items = synth.batch_recipe(synth.BASE_SEED + 3, n=256)
+    srcs, dsts, vs, vd, fs = [], [], [], [], []
+    dt = {synth.U8: torch.uint8, synth.U16: torch.uint16, synth.F32: torch.float32}
+    nbytes = 0
+    for it in items:
+        a = synth.volume(it["kind"], it["fmt"], it["dims"], it["seed"])
+        s = torch.from_numpy(a).to(dev)
+        d = torch.empty(a.shape, dtype=dt[it["fmt"]], device=dev)
+        srcs.append(s)
+        dsts.append(d)
+        vs.append(vkt.StructuredVolume.from_tensor(s))
+        vd.append(vkt.StructuredVolume.from_tensor(d))
+        fs.append(vkt.Filter.gaussian(it["k"], it["sigma"]))
+        nbytes += 2 * a.nbytes
+    vox = float(sum(s.numel() for s in srcs))
+    lib = vkt._lib
+    reps = 5
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        vkt.synchronize()
+        return a.elapsed_time(b) / reps
+
+    with vkt.policy(stream=stream):
+        def batched():
+            vkt.apply_filter_batch(vd, vs, fs, stream=stream)
+
+        def separate():
+            for i in range(len(items)):
+                vkt.check(lib.vktApplyFilterSV(vd[i].handle, vs[i].handle, fs[i].handle))
+
+        ms_batch = timed(batched)
+        ms_sep = timed(separate)
+        # sum of individually timed launches
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in items]
+        for i in range(len(items)):
+            evs[i][0].record(stream)
+            vkt.check(lib.vktApplyFilterSV(vd[i].handle, vs[i].handle, fs[i].handle))
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms_sum = sum(a.elapsed_time(b) for a, b in evs)
+    hbm = measured_peaks()[0]["hbm_gbs"]
+    return {"volumes": len(items), "voxels": int(vox), "algorithmic_bytes": int(nbytes),
+            "graph_batch_ms": round(ms_batch, 4),
+            "graph_batch_gvoxel_s": round(vox / (ms_batch * 1e-3) / 1e9, 2),
+            "graph_batch_frac_hbm": round(nbytes / (ms_batch * 1e-3) / 1e9 / hbm, 4),
+            "separate_back_to_back_ms": round(ms_sep, 4),
+            "separate_sum_of_launches_ms": round(ms_sum, 4),
+            "speedup_vs_back_to_back": round(ms_sep / ms_batch, 3),
+            "speedup_vs_sum_of_launches": round(ms_sum / ms_batch, 3)}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -359,6 +430,9 @@ def run_ours(args):
     pform = None
     if not args.no_precision_form:
         pform = precision_form(args, vkt, torch, dev, stream, peaks)
+    bform = None
+    if not args.no_batching_form:
+        bform = batching_form(args, vkt, torch, dev, stream)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -370,7 +444,7 @@ def run_ours(args):
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clk, "precision_form": pform,
+            "gpu_launches": launches, "clocks": clk, "precision_form": pform, "batching_form": bform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

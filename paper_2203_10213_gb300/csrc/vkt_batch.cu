@@ -1,0 +1,478 @@
+// vkt_batch.cu -- vktApplyFilterBatchSV: many independent (dst, src, filter) triples in one
+// persistent launch over a work list of bricks, captured in a CUDA graph.
+//
+// Separable triples (k <= 7, any source/destination formats, any dims) become bricks of the
+// fused separable pipeline (vkt_sep_brick.cuh): the host builds a per-volume table (data
+// pointers, dims, formats, epilogue constants, the three weight vectors) and one TMA tensor
+// map per volume whose rows allow one (others take the plain-load path), plus a work list of
+// (volume, brick) items ordered by cost.  One CTA per SM slot grabs items from an atomic
+// counter until the list is empty, so uneven volumes balance themselves and there is no
+// per-volume launch.  Dense triples (and separable ones of k = 9, whose registers would
+// slow the whole persistent kernel down) are added to the same graph as single-volume
+// launches of their own path.  The graph (counter reset + persistent kernel + dense launches) is built
+// once per set of handles and replayed while the same handles are passed again; the table is
+// re-uploaded only when weights or value ranges changed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <list>
+#include <mutex>
+#include <vector>
+
+#include "vkt_sep_brick.cuh"
+
+namespace vkt {
+namespace {
+
+// COMP: the work list holds only compensated-mode bricks (integer destinations whose FP32
+// error bound is too loose); each mode gets its own launch so that neither pays the other's
+// registers.
+template <bool COMP>
+__global__ void __launch_bounds__(sep::NT, 2)
+    k_sep_batch(const sep::Job* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
+                const int4* __restrict__ items, int nitems, unsigned* counter, unsigned* status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int next;
+    if (threadIdx.x == 0) sep::init_barriers(smem);
+    __syncthreads();
+    uint32_t gplane = 0;
+    for (;;) {
+        if (threadIdx.x == 0) next = static_cast<int>(atomicAdd(counter, 1u));
+        __syncthreads();
+        const int item = next;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int4 w = items[item];
+        const sep::Job& J = jobs[w.x];
+        const CUtensorMap* tm = maps + w.x;
+        bool ok = true;
+        switch (J.k) {
+#define VKT_BATCH_CASE(KK)                                                                   \
+    case KK: {                                                                               \
+        sep::W<KK> G;                                                                        \
+        for (int i = 0; i < KK; ++i) {                                                       \
+            G.gx[i] = J.g[0][i];                                                             \
+            G.gy[i] = J.g[1][i];                                                             \
+            G.gz[i] = J.g[2][i];                                                             \
+        }                                                                                    \
+        if (COMP)                                                                            \
+            ok = sep::brick_comp<KK>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);         \
+        else                                                                                 \
+            ok = sep::brick<KK>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);              \
+        break;                                                                               \
+    }
+            VKT_BATCH_CASE(1)
+            VKT_BATCH_CASE(3)
+            VKT_BATCH_CASE(5)
+            VKT_BATCH_CASE(7)
+#undef VKT_BATCH_CASE
+        default: break;
+        }
+        if (!ok) break;
+    }
+}
+
+size_t batch_smem(int k, int sfmt, bool comp)
+{
+    if (comp) {
+        switch (k) {
+        case 1: return sep::smem_bytes_comp<1>(sfmt);
+        case 3: return sep::smem_bytes_comp<3>(sfmt);
+        case 5: return sep::smem_bytes_comp<5>(sfmt);
+        default: return sep::smem_bytes_comp<7>(sfmt);
+        }
+    }
+    switch (k) {
+    case 1: return sep::smem_bytes<1>(sfmt);
+    case 3: return sep::smem_bytes<3>(sfmt);
+    case 5: return sep::smem_bytes<5>(sfmt);
+    default: return sep::smem_bytes<7>(sfmt);
+    }
+}
+
+int raw_width(int k, int sfmt)
+{
+    switch (k) {
+    case 1: return Brick<1, sep::TX, sep::TY>::raw_w(sfmt);
+    case 3: return Brick<3, sep::TX, sep::TY>::raw_w(sfmt);
+    case 5: return Brick<5, sep::TX, sep::TY>::raw_w(sfmt);
+    default: return Brick<7, sep::TX, sep::TY>::raw_w(sfmt);
+    }
+}
+
+// A replayable batch: device table, tensor maps, work list, counter, and the graph.
+struct Plan {
+    std::vector<unsigned char> key;
+    int device = -1;
+    void* dmem = nullptr;
+    sep::Job* d_jobs = nullptr;
+    CUtensorMap* d_maps = nullptr;
+    int4* d_items = nullptr;
+    unsigned* d_counter = nullptr;
+    std::vector<sep::Job> jobs;       // table as last uploaded
+    int nitems = 0;
+    unsigned kernels = 0;             // kernels one replay launches
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+
+    void release()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (dmem) cudaFree(dmem);
+        exec = nullptr;
+        graph = nullptr;
+        dmem = nullptr;
+    }
+};
+
+constexpr size_t MAX_PLANS = 4;
+std::mutex g_plans_mutex;
+std::list<Plan> g_plans;   // most recently used first
+
+template <class T>
+void put(std::vector<unsigned char>& key, const T& v)
+{
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&v);
+    key.insert(key.end(), p, p + sizeof(T));
+}
+
+bool valid_volume(const vktStructuredVolume_impl* v) { return v && v->magic == VKT_VOLUME_MAGIC; }
+bool valid_filter(const vktFilter_impl* f) { return f && f->magic == VKT_FILTER_MAGIC; }
+int fbytes(int f) { return f == vktDataFormatUint8 ? 1 : (f == vktDataFormatUint16 ? 2 : 4); }
+double fqmax(int f) { return f == vktDataFormatUint8 ? 255.0 : 65535.0; }
+uint64_t vbytes(const vktStructuredVolume_impl* v)
+{
+    return static_cast<uint64_t>(v->dims[0]) * v->dims[1] * v->dims[2] * fbytes(v->format);
+}
+
+void epilogue_of(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                 double wsum, float* a0, float* a1, float* qmax, float* a0lo = nullptr,
+                 float* a1lo = nullptr)
+{
+    double ls = 0.0, ss = 1.0;
+    if (src->format != vktDataFormatFloat32) {
+        ls = src->lo;
+        ss = (static_cast<double>(src->hi) - src->lo) / fqmax(src->format);
+    }
+    if (dst->format == vktDataFormatFloat32) {
+        *a0 = static_cast<float>(ls * wsum);
+        *a1 = static_cast<float>(ss);
+        *qmax = 0.f;
+    } else {
+        const double sd = fqmax(dst->format) / (static_cast<double>(dst->hi) - dst->lo);
+        *a0 = static_cast<float>((ls * wsum - dst->lo) * sd);
+        *a1 = static_cast<float>(ss * sd);
+        *qmax = static_cast<float>(fqmax(dst->format));
+        if (a0lo) *a0lo = static_cast<float>((ls * wsum - dst->lo) * sd - static_cast<double>(*a0));
+        if (a1lo) *a1lo = static_cast<float>(ss * sd - static_cast<double>(*a1));
+    }
+}
+
+int batch_zchunk(int nz)
+{
+    if (nz <= 96) return nz;
+    const int chunks = (nz + 63) / 64;
+    return (nz + chunks - 1) / chunks;
+}
+
+// sep_idx: triples for the persistent kernel; dense_idx: triples launched on their own
+// (dense filters, and separable ones of k = 9) inside the same graph.
+vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
+                    vktFilter* filters, const std::vector<int>& sep_idx,
+                    const std::vector<int>& dense_idx, bool force_dense, bool force_direct,
+                    const Ctx& ctx)
+{
+    // work list: separable volumes' bricks, heavy kernels first
+    std::vector<int4> items;
+    size_t smem = 0;
+    P.jobs.resize(sep_idx.size());
+    std::vector<CUtensorMap> maps(sep_idx.size());
+    std::vector<std::pair<long, int>> order;
+    for (size_t j = 0; j < sep_idx.size(); ++j) {
+        const int i = sep_idx[j];
+        const vktStructuredVolume_impl* s = src[i];
+        sep::Job& J = P.jobs[j];
+        memset(&J, 0, sizeof(J));
+        J.src = s->data;
+        J.dst = dst[i]->data;
+        J.nx = s->dims[0];
+        J.ny = s->dims[1];
+        J.nz = s->dims[2];
+        J.sfmt = s->format;
+        J.dfmt = dst[i]->format;
+        J.k = filters[i]->k;
+        J.comp = separable_needs_comp(dst[i], s, filters[i]) ? 1 : 0;
+        const int ty = J.comp ? sep::CTY : sep::TY;
+        J.zchunk = batch_zchunk(J.nz);
+        J.tiles_x = (J.nx + sep::TX - 1) / sep::TX;
+        J.tiles_y = (J.ny + ty - 1) / ty;
+        J.chunks = (J.nz + J.zchunk - 1) / J.zchunk;
+        memset(&maps[j], 0, sizeof(CUtensorMap));
+        J.use_tma = encode_tensor_map_3d(&maps[j], J.sfmt, J.src, J.nx, J.ny, J.nz,
+                                         raw_width(J.k, J.sfmt), ty + 2 * ((J.k - 1) / 2), 1)
+                        ? 1
+                        : 0;
+        smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0));
+        order.push_back({-static_cast<long>(J.k) * (J.zchunk + J.k - 1), static_cast<int>(j)});
+    }
+    std::stable_sort(order.begin(), order.end());
+    std::vector<int4> comp_items;
+    size_t smem_fast = 0, smem_comp = 0;
+    for (const auto& o : order) {
+        const sep::Job& J = P.jobs[o.second];
+        std::vector<int4>& dstv = J.comp ? comp_items : items;
+        (J.comp ? smem_comp : smem_fast) = std::max(J.comp ? smem_comp : smem_fast,
+                                                    batch_smem(J.k, J.sfmt, J.comp != 0));
+        for (int bz = 0; bz < J.chunks; ++bz)
+            for (int by = 0; by < J.tiles_y; ++by)
+                for (int bx = 0; bx < J.tiles_x; ++bx) dstv.push_back(make_int4(o.second, bx, by, bz));
+    }
+    const int nfast = static_cast<int>(items.size());
+    const int ncomp = static_cast<int>(comp_items.size());
+    items.insert(items.end(), comp_items.begin(), comp_items.end());
+    P.nitems = static_cast<int>(items.size());
+    (void)smem;
+
+    // one device block: table | maps (64-byte aligned) | items | two counters
+    const size_t njobs = std::max<size_t>(1, P.jobs.size());
+    const size_t off_maps = ((njobs * sizeof(sep::Job)) + 127) & ~size_t(127);
+    const size_t off_items = off_maps + njobs * sizeof(CUtensorMap);
+    const size_t off_counter = off_items + std::max<size_t>(1, items.size()) * sizeof(int4);
+    const size_t total = off_counter + 256;
+    cudaError_t e = cudaMalloc(&P.dmem, total);
+    if (e != cudaSuccess) return from_cuda(e);
+    unsigned char* base = static_cast<unsigned char*>(P.dmem);
+    P.d_jobs = reinterpret_cast<sep::Job*>(base);
+    P.d_maps = reinterpret_cast<CUtensorMap*>(base + off_maps);
+    P.d_items = reinterpret_cast<int4*>(base + off_items);
+    P.d_counter = reinterpret_cast<unsigned*>(base + off_counter);
+    if (!P.jobs.empty()) {
+        e = cudaMemcpy(P.d_jobs, P.jobs.data(), P.jobs.size() * sizeof(sep::Job), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(P.d_maps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpy(P.d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device);
+    int grid_fast = 0, grid_comp = 0;
+    if (nfast > 0) {
+        e = cudaFuncSetAttribute(k_sep_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem_fast));
+        if (e != cudaSuccess) return from_cuda(e);
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<false>, sep::NT, smem_fast);
+        grid_fast = static_cast<int>(std::min<long>(nfast, static_cast<long>(sms) * std::max(per_sm, 1)));
+    }
+    if (ncomp > 0) {
+        e = cudaFuncSetAttribute(k_sep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem_comp));
+        if (e != cudaSuccess) return from_cuda(e);
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<true>, sep::NT, smem_comp);
+        grid_comp = static_cast<int>(std::min<long>(ncomp, static_cast<long>(sms) * std::max(per_sm, 1)));
+    }
+
+    // capture: counter reset + persistent kernel + dense triples on their own paths
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return from_cuda(e);
+    Ctx cctx = ctx;
+    cctx.stream = cs;
+    uint64_t before = 0;
+    vktGetLaunchCount(&before);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    vktError err = from_cuda(e);
+    unsigned kernels = 0;
+    if (err == VKT_NO_ERROR && P.nitems > 0) {
+        e = cudaMemsetAsync(P.d_counter, 0, 2 * sizeof(unsigned), cs);
+        if (e == cudaSuccess && nfast > 0) {
+            k_sep_batch<false><<<grid_fast, sep::NT, smem_fast, cs>>>(P.d_jobs, P.d_maps, P.d_items,
+                                                                      nfast, P.d_counter, ctx.status);
+            e = cudaGetLastError();
+            ++kernels;
+        }
+        if (e == cudaSuccess && ncomp > 0) {
+            k_sep_batch<true><<<grid_comp, sep::NT, smem_comp, cs>>>(P.d_jobs, P.d_maps,
+                                                                     P.d_items + nfast, ncomp,
+                                                                     P.d_counter + 1, ctx.status);
+            e = cudaGetLastError();
+            ++kernels;
+        }
+        err = from_cuda(e);
+    }
+    for (size_t q = 0; q < dense_idx.size() && err == VKT_NO_ERROR; ++q) {
+        const int i = dense_idx[q];
+        const vktFilter_impl* f = filters[i];
+        Job job;
+        job.src = src[i]->data;
+        job.dst = dst[i]->data;
+        job.nx = src[i]->dims[0];
+        job.ny = src[i]->dims[1];
+        job.nz = src[i]->dims[2];
+        job.sfmt = src[i]->format;
+        job.dfmt = dst[i]->format;
+        double wsum = 0.0;
+        const bool sepf = f->separable && !force_dense;
+        if (sepf) {
+            double s3[3] = {0, 0, 0};
+            for (int a = 0; a < 3; ++a)
+                for (int t = 0; t < f->k; ++t) s3[a] += f->g[a][t];
+            wsum = s3[0] * s3[1] * s3[2];
+        } else {
+            for (int t = 0; t < f->k * f->k * f->k; ++t) wsum += f->w[t];
+        }
+        epilogue_of(dst[i], src[i], wsum, &job.a0, &job.a1, &job.qmax, &job.a0lo, &job.a1lo);
+        job.comp = sepf && separable_needs_comp(dst[i], src[i], f) ? 1 : 0;
+        if (sepf)
+            err = launch_separable(job, f->g[0], f->g[1], f->g[2], f->k, cctx);
+        else if (f->k >= 5 && !force_direct && tensor_available(dst[i], src[i], f) == VKT_NO_ERROR)
+            err = launch_tensor(job, f->w, f->k, cctx);
+        else
+            err = launch_direct(job, f->w, f->k, cctx);
+        ++kernels;
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cs, &graph);
+    if (err == VKT_NO_ERROR) err = from_cuda(e);
+    cudaStreamDestroy(cs);
+    uint64_t after = 0;
+    vktGetLaunchCount(&after);
+    uncount_launches(static_cast<unsigned>(after - before));   // captured, not launched
+    if (err != VKT_NO_ERROR) {
+        if (graph) cudaGraphDestroy(graph);
+        return err;
+    }
+    P.graph = graph;
+    e = cudaGraphInstantiate(&P.exec, graph, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    P.kernels = kernels;
+    if (ctx.debug)
+        fprintf(stderr, "[vkt] batch plan: %zu separable volumes, %d + %d compensated bricks, "
+                "grids %d / %d, %zu single launches\n", P.jobs.size(), nfast, ncomp, grid_fast,
+                grid_comp, dense_idx.size());
+    return VKT_NO_ERROR;
+}
+
+}  // namespace
+}  // namespace vkt
+
+using namespace vkt;
+
+extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
+                                          vktFilter* filters)
+{
+    if (n < 1 || !dst || !src || !filters) return VKT_ERROR_INVALID_VALUE;
+    for (int i = 0; i < n; ++i) {
+        if (!valid_volume(dst[i]) || !valid_volume(src[i]) || !valid_filter(filters[i]))
+            return VKT_ERROR_INVALID_HANDLE;
+        for (int a = 0; a < 3; ++a)
+            if (dst[i]->dims[a] != src[i]->dims[a]) return VKT_ERROR_DIMS_MISMATCH;
+        const char* pd = static_cast<const char*>(dst[i]->data);
+        const char* ps = static_cast<const char*>(src[i]->data);
+        if (pd < ps + vbytes(src[i]) && ps < pd + vbytes(dst[i])) return VKT_ERROR_INVALID_VALUE;
+    }
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+    vktExecutionPolicy pol;
+    vktGetThreadExecutionPolicy(&pol);
+    int dev = 0;
+    cudaGetDevice(&dev);
+
+    std::vector<int> sep_idx, dense_idx;
+    std::vector<unsigned char> key;
+    put(key, dev);
+    put(key, n);
+    put(key, pol.path);
+    for (int i = 0; i < n; ++i) {
+        const bool s = filters[i]->separable && filters[i]->k <= 7 && pol.path != VKT_PATH_DIRECT &&
+                       pol.path != VKT_PATH_TENSOR;
+        (s ? sep_idx : dense_idx).push_back(i);
+        put(key, s);
+        put(key, dst[i]->data);
+        put(key, src[i]->data);
+        put(key, src[i]->dims);
+        put(key, src[i]->format);
+        put(key, dst[i]->format);
+        put(key, filters[i]->k);
+        put(key, s && separable_needs_comp(dst[i], src[i], filters[i]));
+        if (!s) {
+            // dense launches bake weights and ranges into the graph
+            key.insert(key.end(), reinterpret_cast<const unsigned char*>(filters[i]->w),
+                       reinterpret_cast<const unsigned char*>(filters[i]->w) +
+                           sizeof(float) * filters[i]->k * filters[i]->k * filters[i]->k);
+            put(key, src[i]->lo);
+            put(key, src[i]->hi);
+            put(key, dst[i]->lo);
+            put(key, dst[i]->hi);
+        }
+    }
+    // current table contents (weights and epilogue constants of the separable volumes)
+    std::vector<sep::Job> table(sep_idx.size());
+    for (size_t j = 0; j < sep_idx.size(); ++j) {
+        const int i = sep_idx[j];
+        const vktFilter_impl* f = filters[i];
+        sep::Job& J = table[j];
+        memset(&J, 0, sizeof(J));
+        double s3[3] = {0, 0, 0};
+        for (int a = 0; a < 3; ++a)
+            for (int t = 0; t < f->k; ++t) {
+                J.g[a][t] = f->g[a][t];
+                s3[a] += f->g[a][t];
+            }
+        epilogue_of(dst[i], src[i], s3[0] * s3[1] * s3[2], &J.a0, &J.a1, &J.qmax, &J.a0lo, &J.a1lo);
+        J.comp = separable_needs_comp(dst[i], src[i], f) ? 1 : 0;
+    }
+
+    std::lock_guard<std::mutex> lock(g_plans_mutex);
+    auto it = std::find_if(g_plans.begin(), g_plans.end(), [&](const Plan& p) { return p.key == key; });
+    if (it == g_plans.end()) {
+        Plan P;
+        P.key = key;
+        P.device = dev;
+        err = build_plan(P, n, dst, src, filters, sep_idx, dense_idx,
+                         pol.path == VKT_PATH_DIRECT || pol.path == VKT_PATH_TENSOR,
+                         pol.path == VKT_PATH_DIRECT, ctx);
+        if (err != VKT_NO_ERROR) {
+            P.release();
+            return err;
+        }
+        g_plans.push_front(std::move(P));
+        while (g_plans.size() > MAX_PLANS) {
+            g_plans.back().release();
+            g_plans.pop_back();
+        }
+        it = g_plans.begin();
+    } else if (it != g_plans.begin()) {
+        g_plans.splice(g_plans.begin(), g_plans, it);
+        it = g_plans.begin();
+    }
+    Plan& P = *it;
+    cudaStream_t stream = static_cast<cudaStream_t>(pol.stream);
+    // refresh weights / epilogue constants where they changed since the last upload
+    for (size_t j = 0; j < table.size(); ++j) {
+        sep::Job& J = P.jobs[j];
+        if (memcmp(J.g, table[j].g, sizeof(J.g)) != 0 || J.a0 != table[j].a0 ||
+            J.a1 != table[j].a1 || J.qmax != table[j].qmax || J.a0lo != table[j].a0lo ||
+            J.a1lo != table[j].a1lo) {
+            memcpy(J.g, table[j].g, sizeof(J.g));
+            J.a0 = table[j].a0;
+            J.a1 = table[j].a1;
+            J.qmax = table[j].qmax;
+            J.a0lo = table[j].a0lo;
+            J.a1lo = table[j].a1lo;
+            cudaError_t e = cudaMemcpyAsync(P.d_jobs + j, &J, sizeof(sep::Job),
+                                            cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(P.exec, stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    count_launches(P.kernels);
+    return VKT_NO_ERROR;
+}

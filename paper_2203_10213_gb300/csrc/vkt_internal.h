@@ -38,6 +38,11 @@ struct Job {
     // Epilogue: the kernels accumulate acc = sum w * q over stored source values q and
     // write a0 + a1*acc (float dst), or clamp(rint(a0 + a1*acc), 0, qmax) (integer dst).
     float a0, a1, qmax;
+    // Compensated accumulation (separable path, integer destinations): set when an FP32
+    // error bound does not keep the code within 1e-3 LSB of exact; a0lo/a1lo carry the
+    // low halves of a0/a1 as double-float pairs.
+    int comp;
+    float a0lo, a1lo;
 };
 
 struct Ctx {
@@ -64,9 +69,14 @@ vktError tensor_available(const vktStructuredVolume_impl* dst, const vktStructur
                           const vktFilter_impl* f);
 vktError launch_tensor(const Job& job, const float* w, int k, const Ctx& ctx);
 
+// Whether a separable filter into an integer destination needs compensated accumulation.
+bool separable_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                          const vktFilter_impl* f);
+
 // Helpers provided by the runtime.
 vktError get_context(Ctx* ctx);
 void count_launches(unsigned n);
+void uncount_launches(unsigned n);   // launches that were captured into a graph, not run
 vktError from_cuda(cudaError_t e);
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 bool encode_tensor_map_3d(void* map /* CUtensorMap* */, int fmt, const void* base, int nx,

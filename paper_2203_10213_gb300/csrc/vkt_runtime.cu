@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -92,6 +93,7 @@ bool overlaps(const vktStructuredVolume_impl* a, const vktStructuredVolume_impl*
 // stored values q (codes for integer sources); the mapped result is
 //   v = lo_s * W + s_s * acc,   W = sum of the weights, s_s = (hi_s - lo_s)/(2^N - 1)
 // and an integer destination stores clamp(rint((v - lo_d) * (2^M - 1)/(hi_d - lo_d))).
+// a0 + a1 * acc is that destination value (or code); the low halves give double-float pairs.
 void epilogue(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
               double wsum, Job* job)
 {
@@ -100,16 +102,22 @@ void epilogue(const vktStructuredVolume_impl* dst, const vktStructuredVolume_imp
         ls = src->lo;
         ss = (static_cast<double>(src->hi) - src->lo) / fmt_qmax(src->format);
     }
+    double a0, a1;
     if (dst->format == vktDataFormatFloat32) {
-        job->a0 = static_cast<float>(ls * wsum);
-        job->a1 = static_cast<float>(ss);
+        a0 = ls * wsum;
+        a1 = ss;
         job->qmax = 0.f;
     } else {
         const double sd = fmt_qmax(dst->format) / (static_cast<double>(dst->hi) - dst->lo);
-        job->a0 = static_cast<float>((ls * wsum - dst->lo) * sd);
-        job->a1 = static_cast<float>(ss * sd);
+        a0 = (ls * wsum - dst->lo) * sd;
+        a1 = ss * sd;
         job->qmax = static_cast<float>(fmt_qmax(dst->format));
     }
+    job->a0 = static_cast<float>(a0);
+    job->a1 = static_cast<float>(a1);
+    job->a0lo = static_cast<float>(a0 - static_cast<double>(job->a0));
+    job->a1lo = static_cast<float>(a1 - static_cast<double>(job->a1));
+    job->comp = 0;
 }
 
 }  // namespace
@@ -142,7 +150,27 @@ vktError get_context(Ctx* ctx)
     return VKT_NO_ERROR;
 }
 
+// Whether a separable filter into an integer destination needs compensated accumulation:
+// an FP32 evaluation of the three passes (3k + 4 roundings, each at most 2^-24 of a value
+// bounded by sum|gx| sum|gy| sum|gz| max|v|) must stay below 5e-4 of a destination code, or
+// a rounding decision outside the 1e-3 LSB tie window could flip.  A float32 source has no
+// known bound on |v| and always takes the compensated path.
+bool separable_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                          const vktFilter_impl* f)
+{
+    if (dst->format == vktDataFormatFloat32) return false;
+    if (src->format == vktDataFormatFloat32) return true;
+    double s[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < f->k; ++i) s[a] += std::fabs(static_cast<double>(f->g[a][i]));
+    const double vmax = std::max(std::fabs(static_cast<double>(src->lo)), std::fabs(static_cast<double>(src->hi)));
+    const double sd = fmt_qmax(dst->format) / std::fabs(static_cast<double>(dst->hi) - dst->lo);
+    const double bound = (3.0 * f->k + 4.0) * std::ldexp(1.0, -24) * s[0] * s[1] * s[2] * vmax * sd;
+    return bound >= 5e-4;
+}
+
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 vktError from_cuda(cudaError_t e)
 {
@@ -595,6 +623,7 @@ vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktF
         for (int i = 0; i < k * k * k; ++i) wsum += filter->w[i];
     }
     epilogue(dst, src, wsum, &job);
+    if (path == VKT_PATH_SEPARABLE) job.comp = separable_needs_comp(dst, src, filter) ? 1 : 0;
 
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (t_policy.printTimes) {

@@ -36,6 +36,9 @@ struct Job {
     int tiles_x, tiles_y, chunks;
     float a0, a1, qmax;
     float g[3][VKT_MAX_FILTER_SIZE];    // x, y, z vectors
+    // compensated mode (integer destinations): epilogue constants as double-float pairs
+    int comp;
+    float a0lo, a1lo;
 };
 
 template <int K>
@@ -60,9 +63,9 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
     fence_mbar_init();
 }
 
-// Runs brick (bx, by, bz) of job J.  `gplane` counts the planes this CTA has pipelined so
-// far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring carries on
-// across bricks.  Returns false if a bounded wait timed out (after recording it and
+// Runs brick (bx, by, bz) of job J.  `gplane` counts the planes this CTA has brought in by
+// TMA so far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring and its
+// barrier phases carry on across bricks.  Returns false if a bounded wait timed out (after recording it and
 // draining the loads in flight).
 template <int K, class Wt>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
@@ -213,8 +216,224 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             plane(it, u);
         }
     }
-    gplane = g0 + nplanes;
+    // only TMA bricks move the stage barriers through their phases
+    if (J.use_tma) gplane = g0 + nplanes;
 
+    if (failed) {
+        if (tid == 0) {
+            atomicOr(status, STATUS_TIMEOUT);
+            for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
+                mbar_wait(&bars[(g0 + it) % STAGES], ((g0 + it) / STAGES) & 1);
+        }
+        __syncthreads();
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Compensated variant for integer destinations.  An FP32 sum of k taps per pass leaves an
+// error of ~1e-2 of a 16-bit code, more than the 1e-3 LSB within which a rounding tie may
+// go either way, so every pass carries a double-float (hi, lo) value built from error-free
+// transformations: TwoProd(a,b) = (a*b, fma(a,b,-a*b)) and Knuth's TwoSum, accumulated as
+// in the compensated dot product Dot2 (Ogita, Rump, Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 2005).  The epilogue maps (hi, lo) to the code value in double-float
+// and takes the rounding decision on the pair.  One output row per thread (RY = 1) keeps the
+// 2 x k x 4 accumulators in registers.
+
+constexpr int CRY = 1;
+constexpr int CTY = BY * CRY;
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, c) += g * (h + l), with the product's rounding error recovered exactly
+__device__ __forceinline__ void dot2_step(float g, float h, float l, float& s, float& c)
+{
+    const float p = __fmul_rn(g, h);
+    float e = __fmaf_rn(g, h, -p);
+    e = __fmaf_rn(g, l, e);
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+// code = clamp(round-half-even(a0 + a1 * (s + c)), 0, qmax) with a0, a1 double-float
+__device__ __forceinline__ unsigned comp_code(float s, float c, float a0h, float a0l, float a1h,
+                                              float a1l, float qmax)
+{
+    const float p = __fmul_rn(a1h, s);
+    float e = __fmaf_rn(a1h, s, -p);
+    e = __fmaf_rn(a1h, c, e);
+    e = __fmaf_rn(a1l, s, e);
+    float u, t;
+    two_sum(a0h, p, u, t);
+    const float lo = __fadd_rn(__fadd_rn(t, e), a0l);
+    if (!(fabsf(u) < 1.0e9f)) return u > 0.f ? static_cast<unsigned>(qmax) : 0u;   // NaN -> 0
+    float q = rintf(u);
+    const float r = __fadd_rn(__fsub_rn(u, q), lo);   // u - q is exact
+    if (r > 0.5f) q += 1.f;
+    else if (r < -0.5f) q -= 1.f;
+    else if (r == 0.5f || r == -0.5f) {
+        const float cand = r > 0.f ? q + 1.f : q - 1.f;     // exact tie: the even code
+        if (fmodf(cand, 2.f) == 0.f) q = cand;
+    }
+    return static_cast<unsigned>(fminf(fmaxf(q, 0.f), qmax));
+}
+
+template <int K>
+__host__ __device__ constexpr size_t smem_bytes_comp(int sfmt)
+{
+    using Geo = Brick<K, TX, CTY>;
+    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+           static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +
+           static_cast<size_t>(Geo::FH) * TX * sizeof(float2);           // (hi, lo) x pass
+}
+
+template <int K, class Wt>
+__device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUtensorMap* tmap,
+                                           int bx, int by, int bz, unsigned char* smem,
+                                           uint32_t& gplane, unsigned* status)
+{
+    using Geo = Brick<K, TX, CTY>;
+    constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
+    constexpr int XGROUPS = TX / 4;
+    constexpr int XITEMS = FH * XGROUPS;
+
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    const int rawb = Geo::raw_bytes(J.sfmt);
+    const uint32_t txb = Geo::raw_tx(J.sfmt);
+    unsigned char* raw = smem + 128;
+    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+    float2* T1 = reinterpret_cast<float2*>(F + FH * FP);
+
+    const int tid = threadIdx.x;
+    const int tx = tid % BX, ty = tid / BX;
+    const int x0 = bx * TX, y0 = by * CTY;
+    const int zc0 = bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, J.nz);
+    if (zc0 >= zc1) return true;
+    const int pfirst = zc0 - R;
+    const int nplanes = zc1 - zc0 + 2 * R;
+    const int xa = fmt_xalign(J.sfmt);
+    const uint32_t g0 = gplane;
+
+    int issued = 0;
+    if (J.use_tma && tid == 0) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+            const uint32_t q = g0 + s;
+            mbar_arrive_expect_tx(&bars[q % STAGES], txb);
+            tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
+                        clampi(pfirst + s, 0, J.nz - 1));
+        }
+    }
+    ConvPlan<Geo, NT> plan;
+    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid);
+
+    float acc_s[K][RX], acc_c[K][RX];
+#pragma unroll
+    for (int s = 0; s < K; ++s)
+#pragma unroll
+        for (int x = 0; x < RX; ++x) acc_s[s][x] = acc_c[s][x] = 0.f;
+
+    const int ox = x0 + tx * RX;
+    const int oy = y0 + ty;
+    const int nvalid = J.nx - ox;
+    bool failed = false;
+
+    auto plane = [&](const int it, const int u) {
+        const uint32_t q = g0 + it;
+        const int s = q % STAGES;
+        const unsigned char* rs = raw + s * rawb;
+        bool ok = true;
+        if (J.use_tma) {
+            ok = mbar_wait(&bars[s], (q / STAGES) & 1);
+        } else {
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, J.sfmt, J.nx, J.ny,
+                                    J.nz, x0, y0, pfirst + it, tid);
+            __syncthreads();
+        }
+        if (ok) plan.convert(rs, J.sfmt, F, tid);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            return;
+        }
+        if (J.use_tma && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive_expect_tx(&bars[s], txb);
+            tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(pfirst + it + STAGES, 0, J.nz - 1));
+            ++issued;
+        }
+        // x pass (inputs exact): T1[row][x] = Dot2(gx, F[row][x .. x+k-1])
+#pragma unroll
+        for (int n = 0; n < (XITEMS + NT - 1) / NT; ++n) {
+            const int item = tid + n * NT;
+            if (item < XITEMS) {
+                const int row = item / XGROUPS, g = item - row * XGROUPS;
+                float win[4 + K - 1];
+                load_row<4 + K - 1, 4>(F + row * FP + 4 * g, win);
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    float hs = 0.f, hc = 0.f;
+#pragma unroll
+                    for (int a = 0; a < K; ++a) dot2_step(G.gx[a], win[x + a], 0.f, hs, hc);
+                    T1[row * TX + 4 * g + x] = make_float2(hs, hc);
+                }
+            }
+        }
+        __syncthreads();
+        // y pass on the (hi, lo) pairs, then the z pass into the K rotating pair accumulators
+        float ts[RX], tc[RX];
+#pragma unroll
+        for (int x = 0; x < RX; ++x) ts[x] = tc[x] = 0.f;
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const float2* r = T1 + (ty + b) * TX + tx * RX;
+#pragma unroll
+            for (int x = 0; x < RX; ++x) {
+                const float2 v = r[x];
+                dot2_step(G.gy[b], v.x, v.y, ts[x], tc[x]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const int sl = ((u - c + R) % K + K) % K;
+#pragma unroll
+            for (int x = 0; x < RX; ++x) dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
+        }
+        const int sl0 = ((u - R) % K + K) % K;
+        if (it >= 2 * R && oy < J.ny && nvalid > 0) {
+            const int oz = pfirst + it - R;
+            const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
+#pragma unroll
+            for (int x = 0; x < RX; ++x) {
+                if (x < nvalid) {
+                    const unsigned code = comp_code(acc_s[sl0][x], acc_c[sl0][x], J.a0, J.a0lo,
+                                                    J.a1, J.a1lo, J.qmax);
+                    if (J.dfmt == FMT_U16)
+                        reinterpret_cast<uint16_t*>(J.dst)[idx + x] = static_cast<uint16_t>(code);
+                    else
+                        reinterpret_cast<unsigned char*>(J.dst)[idx + x] = static_cast<unsigned char>(code);
+                }
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < RX; ++x) acc_s[sl0][x] = acc_c[sl0][x] = 0.f;
+    };
+
+    for (int g = 0; g * K < nplanes && !failed; ++g) {
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int it = g * K + u;
+            if (it >= nplanes || failed) break;
+            plane(it, u);
+        }
+    }
+    if (J.use_tma) gplane = g0 + nplanes;
     if (failed) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);

@@ -26,6 +26,21 @@ __global__ void __launch_bounds__(sep::NT)
 }
 
 template <int K>
+__global__ void __launch_bounds__(sep::NT)
+    k_separable_comp(const __grid_constant__ CUtensorMap tmap, const sep::Job J,
+                     const sep::W<K> G, unsigned* status)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) {
+        sep::init_barriers(smem);
+        if (J.use_tma) prefetch_tensor_map(&tmap);
+    }
+    __syncthreads();
+    uint32_t gplane = 0;
+    sep::brick_comp<K>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem, gplane, status);
+}
+
+template <int K>
 vktError launch_k(const Job& job, const float* gx, const float* gy, const float* gz,
                   const Ctx& ctx)
 {
@@ -43,6 +58,10 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     J.a0 = job.a0;
     J.a1 = job.a1;
     J.qmax = job.qmax;
+    J.comp = job.comp;
+    J.a0lo = job.a0lo;
+    J.a1lo = job.a1lo;
+    const int ty = J.comp ? sep::CTY : sep::TY;
     sep::W<K> G;
     for (int i = 0; i < K; ++i) {
         G.gx[i] = gx[i];
@@ -57,25 +76,32 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     }
     J.zchunk = sep::choose_zchunk(job.nx, job.ny, job.nz, sms);
     J.tiles_x = (job.nx + sep::TX - 1) / sep::TX;
-    J.tiles_y = (job.ny + sep::TY - 1) / sep::TY;
+    J.tiles_y = (job.ny + ty - 1) / ty;
     J.chunks = (job.nz + J.zchunk - 1) / J.zchunk;
 
     alignas(64) CUtensorMap map;
     J.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz,
-                                     Geo::raw_w(job.sfmt), Geo::FH, 1)
+                                     Geo::raw_w(job.sfmt), ty + 2 * Geo::R, 1)
                     ? 1
                     : 0;
     if (!J.use_tma) memset(&map, 0, sizeof(map));
-    const size_t smem = sep::smem_bytes<K>(job.sfmt);
-    cudaError_t e = cudaFuncSetAttribute(k_separable<K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt) : sep::smem_bytes<K>(job.sfmt);
+    cudaError_t e = J.comp ? cudaFuncSetAttribute(k_separable_comp<K>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem))
+                           : cudaFuncSetAttribute(k_separable<K>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
     if (ctx.debug)
-        fprintf(stderr, "[vkt] separable k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n", K,
-                J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem, J.use_tma);
-    k_separable<K><<<dim3(J.tiles_x, J.tiles_y, J.chunks), sep::NT, smem, ctx.stream>>>(map, J, G,
-                                                                                      ctx.status);
+        fprintf(stderr, "[vkt] separable%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
+                J.comp ? "-compensated" : "", K, J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem,
+                J.use_tma);
+    const dim3 grid(J.tiles_x, J.tiles_y, J.chunks);
+    if (J.comp)
+        k_separable_comp<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
+    else
+        k_separable<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
     count_launches(1);
     return from_cuda(cudaGetLastError());
 }

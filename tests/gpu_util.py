@@ -51,7 +51,8 @@ def compare(gpu: np.ndarray, ref: np.ndarray, w, src: np.ndarray, src_range, dst
                            f"first at {np.flatnonzero(bad)[:5]}, gpu {g[bad][:5]}, "
                            f"oracle {q[bad][:5]}, t {t.ravel()[bad][:5]}")
     tg = g[tie]
+    qmax = 255 if fmt == oracle.U8 else 65535
     lo_ok = np.floor(t.ravel()[tie]).astype(np.int64)
-    ok = (tg == np.clip(lo_ok, 0, None)) | (tg == lo_ok + 1)
+    ok = (tg == np.clip(lo_ok, 0, qmax)) | (tg == np.clip(lo_ok + 1, 0, qmax))
     assert ok.all(), f"{what}: tie voxels outside the two neighbouring codes"
     return 0.0

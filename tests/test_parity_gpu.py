@@ -80,7 +80,7 @@ def test_separable_f32(shape, k):
 
 
 @pytest.mark.parametrize("sfmt", [synth.U8, synth.U16, synth.F32])
-@pytest.mark.parametrize("dfmt", [synth.U8, synth.F32])
+@pytest.mark.parametrize("dfmt", [synth.U8, synth.U16, synth.F32])
 def test_separable_gaussian_format_pairs(sfmt, dfmt):
     k, sigma = 5, 1.5
     shape = SHAPES[0] if (sfmt + dfmt) % 2 == 0 else SHAPES[1]
@@ -90,6 +90,21 @@ def test_separable_gaussian_format_pairs(sfmt, dfmt):
     w = oracle.gaussian_weights(k, sigma)
     ref = oracle.correlate(src, w, *srange)
     compare(gpu, ref, w, src, srange, drange, f"gaussian {sfmt}->{dfmt}")
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 9])
+def test_separable_uint16_destination_exact(k):
+    """uint16 codes bit-exact outside the 1e-3 LSB tie window (compensated accumulation),
+    with signed weights and shifted ranges."""
+    shape = SHAPES[k % 2]
+    src = src_volume(synth.U16, shape, SEED + 90 + k)
+    g = [synth.normal(SEED + 95 + k + i, (k,), 0.3, 1.0) for i in range(3)]
+    f = vkt.Filter.separable(*g)
+    srange, drange = (-1.0, 3.0), (-4.0, 9.0)
+    gpu = run_gpu(vkt, src, f, torch.uint16, srange, drange, path="separable")
+    w = oracle.separable_weights(*g)
+    ref = oracle.correlate(src, w, *srange)
+    compare(gpu, ref, w, src, srange, drange, f"u16 dst k={k}")
 
 
 EDGE_SHAPES = [(1, 1, 1), (1, 7, 3), (2, 3, 4), (1, 1, 1000), (300, 3, 5), (3, 260, 2)]

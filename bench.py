@@ -48,7 +48,56 @@ def parse():
     ap.add_argument("--precision-reps", type=int, default=10)
     ap.add_argument("--no-batching-form", action="store_true",
                     help="skip the 256-volume graph batch vs separate launches comparison")
+    ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES),
+                    help="run one kernel configuration --reps times and exit (for ncu captures)")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
+
+
+# single-kernel cases for profiler captures: (value model, format, dims, filter, path)
+KERNEL_CASES = {
+    "sep5_ct512": ("blobs", 0, (512, 512, 512), "gaussian5", "separable"),
+    "lap3_ct512": ("blobs", 0, (512, 512, 512), "laplacian3", "direct"),
+    "sep5_ct640": ("blobs", 0, (640, 512, 512), "gaussian5", "separable"),
+    "lap3_ct640": ("blobs", 0, (640, 512, 512), "laplacian3", "direct"),
+    "tc7_dns512": ("uniform", 2, (512, 512, 256), "random7", "tensor"),
+    "direct7_dns512": ("uniform", 2, (512, 512, 256), "random7", "direct"),
+}
+
+# Per-launch DRAM traffic of the kernels this bench reports, from the ncu captures summarised
+# in profiles/; each entry holds the hash of the kernel's sources at capture time and is
+# used only while the sources are unchanged.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.md")
+KERNEL_SOURCES = {
+    "separable gaussian5": ["vkt_sep_brick.cuh", "vkt_separable.cu", "vkt_tile.cuh"],
+    "direct laplacian3": ["vkt_direct.cu", "vkt_tile.cuh"],
+}
+
+
+def source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2203_10213_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str):
+    """(bytes per launch at 512^3, capture note) if a current capture exists, else (None, why)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = [ln.strip() for ln in f if ln.startswith("| ") and "source" not in ln]
+    except OSError:
+        return None, "no capture summary"
+    want = source_hash(KERNEL_SOURCES[kernel])
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel:
+            if cells[3] != want:
+                return None, "kernel changed since the capture"
+            return float(cells[1]), cells[2]
+    return None, "kernel not captured"
 
 
 def dist_env():
@@ -414,10 +463,12 @@ def run_ours(args):
                         "frac_hbm": round(gbs / hbm, 4),
                         "gvoxel_s": round(vox / (avg * 1e-3) / 1e9, 2)})
     dom = max(kernels, key=lambda k: k["avg_ms"])
+    traffic, traffic_note = captured_traffic(dom["kernel"])
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["achieved_gbs"],
                 "peak": hbm, "unit": "GB/s", "frac": dom["frac_hbm"],
                 "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
-                "algorithmic_bytes_per_launch": int(alg_bytes), "traffic": None}
+                "algorithmic_bytes_per_launch": int(alg_bytes), "traffic": traffic,
+                "traffic_note": traffic_note}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -489,8 +540,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_kernel_case(args):
+    import torch
+    import oracle
+    import synth
+    import paper_2203_10213_gb300 as vkt
+    kind, fmt, dims, filt, path = KERNEL_CASES[args.kernel_case]
+    if kind == "uniform":
+        vol = synth.uniform(synth.BASE_SEED + 5, tuple(reversed(dims)), -1.0, 1.0)
+    else:
+        vol = synth.volume(kind, fmt, dims, SEED)
+    if filt == "gaussian5":
+        f = vkt.Filter.gaussian(5, 1.5)
+    elif filt == "laplacian3":
+        f = vkt.Filter.dense(oracle.laplacian_3().astype(np.float32))
+    else:
+        w, _ = synth.random_kernel(synth.BASE_SEED + 2, 7, 1.0, normalise_sum=True)
+        f = vkt.Filter.dense(w)
+    src = torch.from_numpy(vol).cuda()
+    out = torch.empty(vol.shape, dtype=torch.float32, device="cuda")
+    for _ in range(args.reps):
+        vkt.filter_tensor(src, f, path=path, out=out)
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    print(json.dumps({"kernel_case": args.kernel_case, "reps": args.reps,
+                      "checksum": float(out.double().abs().mean())}))
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        run_kernel_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -87,7 +87,8 @@ __device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, in
     }
 }
 
-template <int K, bool ADJ>
+// SF/DF: source and destination formats fixed at compile time (-1: read from the arguments)
+template <int K, bool ADJ, int SF = -1, int DF = -1>
 __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
@@ -97,9 +98,11 @@ __global__ void __launch_bounds__(NT)
     constexpr int FH = Geo::FH, FP = Geo::FP;
 
     extern __shared__ __align__(128) unsigned char smem[];
+    const int sfmt = SF >= 0 ? SF : p.sfmt;
+    const int dfmt = DF >= 0 ? DF : p.dfmt;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const int rawb = Geo::raw_bytes(p.sfmt);
-    const uint32_t txb = Geo::raw_tx(p.sfmt);
+    const int rawb = Geo::raw_bytes(sfmt);
+    const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
 
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(NT)
     if (zc0 >= zc1) return;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
-    const int xa = fmt_xalign(p.sfmt);
+    const int xa = fmt_xalign(sfmt);
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(NT)
     }
 
     ConvPlan<Geo, NT, !ADJ> plan;
-    plan.init(p.sfmt, p.nx, p.ny, x0, y0, tid);
+    plan.init(sfmt, p.nx, p.ny, x0, y0, tid);
 
     float acc[K][RY][RX];
 #pragma unroll
@@ -152,11 +155,11 @@ __global__ void __launch_bounds__(NT)
         if (p.use_tma) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
-            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, p.sfmt, p.nx,
+            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, sfmt, p.nx,
                                           p.ny, p.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
-        if (ok) plan.convert(rs, p.sfmt, Fb, tid);
+        if (ok) plan.convert(rs, sfmt, Fb, tid);
         if (__syncthreads_or(!ok)) {
             failed = true;
             return;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(NT)
                                           ox, acc[sl0][i]);
                 } else if (oy < p.ny && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
-                    store_row<RX>(p.dst, p.dfmt, idx, nvalid, acc[sl0][i], p.a0, p.a1, p.qmax);
+                    store_row<RX>(p.dst, dfmt, idx, nvalid, acc[sl0][i], p.a0, p.a1, p.qmax);
                 }
             }
         }
@@ -308,14 +311,19 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     if (!a.use_tma) memset(&map, 0, sizeof(map));
 
     const size_t smem = direct_smem_bytes<K>(job.sfmt);
-    cudaError_t e = cudaFuncSetAttribute(k_direct<K, ADJ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the common float32 destinations get kernels with their formats compiled in
+    auto kern = k_direct<K, ADJ>;
+    if constexpr (!ADJ && K >= 3 && K <= 5) {
+        if (job.dfmt == FMT_F32 && job.sfmt == FMT_U8) kern = k_direct<K, ADJ, FMT_U8, FMT_F32>;
+        if (job.dfmt == FMT_F32 && job.sfmt == FMT_F32) kern = k_direct<K, ADJ, FMT_F32, FMT_F32>;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
     if (ctx.debug)
         fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
                 ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma);
-    k_direct<K, ADJ><<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
+    kern<<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
     count_launches(1);
     return from_cuda(cudaGetLastError());
 }

@@ -67,7 +67,7 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // TMA so far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring and its
 // barrier phases carry on across bricks.  Returns false if a bounded wait timed out (after recording it and
 // draining the loads in flight).
-template <int K, class Wt>
+template <int K, class Wt, int SF = -1, int DF = -1>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
@@ -77,9 +77,12 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     constexpr int XGROUPS = TX / 4;
     constexpr int XITEMS = FH * XGROUPS;
 
+    // formats fixed at compile time (SF, DF >= 0) fold the format branches away
+    const int sfmt = SF >= 0 ? SF : J.sfmt;
+    const int dfmt = DF >= 0 ? DF : J.dfmt;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const int rawb = Geo::raw_bytes(J.sfmt);
-    const uint32_t txb = Geo::raw_tx(J.sfmt);
+    const int rawb = Geo::raw_bytes(sfmt);
+    const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
     float* T1 = F + FH * FP;
@@ -92,7 +95,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     if (zc0 >= zc1) return true;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
-    const int xa = fmt_xalign(J.sfmt);
+    const int xa = fmt_xalign(sfmt);
     const uint32_t g0 = gplane;
 
     int issued = 0;
@@ -106,7 +109,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     }
 
     ConvPlan<Geo, NT> plan;
-    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid);
+    plan.init(sfmt, J.nx, J.ny, x0, y0, tid);
 
     float acc[K][RY][RX];
 #pragma unroll
@@ -128,11 +131,11 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         if (J.use_tma) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
-            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, J.sfmt, J.nx, J.ny,
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, sfmt, J.nx, J.ny,
                                     J.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
-        if (ok) plan.convert(rs, J.sfmt, F, tid);
+        if (ok) plan.convert(rs, sfmt, F, tid);
         if (__syncthreads_or(!ok)) {
             failed = true;
             return;
@@ -198,7 +201,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
                 const int oy = y0 + ty * RY + i;
                 if (oy < J.ny && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
-                    store_row<RX>(J.dst, J.dfmt, idx, nvalid, acc[sl0][i], J.a0, J.a1, J.qmax);
+                    store_row<RX>(J.dst, dfmt, idx, nvalid, acc[sl0][i], J.a0, J.a1, J.qmax);
                 }
             }
         }

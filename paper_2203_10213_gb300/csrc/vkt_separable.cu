@@ -10,8 +10,14 @@
 namespace vkt {
 namespace {
 
-template <int K>
-__global__ void __launch_bounds__(sep::NT)
+// CTAs per SM the register allocation must allow; format-specialised kernels keep more of
+// their plane loop in registers and get two
+template <int K, int SF>
+constexpr int sep_min_blocks() { return (K <= 5 && SF < 0) ? 3 : 2; }
+
+// SF/DF: source and destination formats fixed at compile time (-1: read from the job)
+template <int K, int SF = -1, int DF = -1>
+__global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     k_separable(const __grid_constant__ CUtensorMap tmap, const sep::Job J, const sep::W<K> G,
                 unsigned* status)
 {
@@ -22,7 +28,8 @@ __global__ void __launch_bounds__(sep::NT)
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick<K>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem, gplane, status);
+    sep::brick<K, sep::W<K>, SF, DF>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
+                                     gplane, status);
 }
 
 template <int K>
@@ -86,10 +93,16 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                     : 0;
     if (!J.use_tma) memset(&map, 0, sizeof(map));
     const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt) : sep::smem_bytes<K>(job.sfmt);
+    // the common float32 destinations get kernels with their formats compiled in
+    auto fast = k_separable<K>;
+    if constexpr (K >= 3 && K <= 7) {
+        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_U8) fast = k_separable<K, FMT_U8, FMT_F32>;
+        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_F32) fast = k_separable<K, FMT_F32, FMT_F32>;
+    }
     cudaError_t e = J.comp ? cudaFuncSetAttribute(k_separable_comp<K>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem))
-                           : cudaFuncSetAttribute(k_separable<K>,
+                           : cudaFuncSetAttribute(fast,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
@@ -101,7 +114,7 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     if (J.comp)
         k_separable_comp<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
     else
-        k_separable<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
+        fast<<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
     count_launches(1);
     return from_cuda(cudaGetLastError());
 }

@@ -48,11 +48,19 @@ struct TcCfg {
     static constexpr int ROWS = MROWS + 2 * R;            // input rows of a plane tile
     static constexpr int SLOTS = ((K + 1) / 2) * 2;       // even, so N is a multiple of 16
     static constexpr int N = SLOTS * 8;
-    static constexpr int TMEM_COLS = (2 * XT * N <= 256) ? 256 : 512;
+    // CAT: the hi*hi and hi*lo products share one MMA of width 2N over the stacked
+    // operand [T_hi | T_lo], so A_hi is read once per (dy, x tile); the D columns [0,N)
+    // then hold hi*hi + lo*hi and [N,2N) hold hi*lo.  Measured slower on GB300 (the
+    // epilogue reads twice the columns), so it is off.
+    static constexpr bool CAT = false;
+    static constexpr int DN = CAT ? 2 * N : N;          // TMEM columns per (buffer, x tile)
+    static constexpr int DBUF = 3;                       // TMEM accumulator buffers
+    static_assert(DBUF * XT * DN <= 512, "TMEM holds 512 columns");
+    static constexpr int TMEM_COLS = (DBUF * XT * DN <= 256) ? 256 : 512;
     static constexpr int STAGE_BYTES = ((ROWS * NCH * 8 * 4) + 1023) & ~1023;
     static constexpr int STAGE_TX = ROWS * NCH * 8 * 4;
     static constexpr int OP_BYTES = ((NCH * ROWS * 16) + 1023) & ~1023;   // one fp16 plane
-    static constexpr int B_BYTES = 2 * N * 16;                            // one Toeplitz
+    static constexpr int B_BYTES = 2 * N * 16;                            // one Toeplitz (hi or lo)
     static constexpr int UNITS = NCH * ROWS;                              // (chunk,row) units
     static constexpr int UPT = (UNITS + NCONV - 1) / NCONV;               // units per thread
     // shared memory map
@@ -81,14 +89,14 @@ struct TcHeader {
     uint64_t stage_empty[STAGES];
     uint64_t op_full[2];
     uint64_t op_empty[2];
-    uint64_t d_full[2];
-    uint64_t d_free[2];
+    uint64_t d_full[3];
+    uint64_t d_free[3];
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
     int conv_ok;
     int sc[SC_RING];     // per-plane scale exponents written by the converters
-    int dsc[2];          // scale exponent of the plane in each TMEM buffer
+    int dsc[3];          // scale exponent of the plane in each TMEM buffer
     float red[2][4];     // converter max reduction
 };
 static_assert(sizeof(TcHeader) <= 1024, "header");
@@ -141,6 +149,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns of this warp's 32 lanes into v[0..15]; complete after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v)
+{
+    uint32_t* r = reinterpret_cast<uint32_t*>(v);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void named_sync(int id, int n)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -185,6 +208,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int b = 0; b < 2; ++b) {
             mbar_init(&h.op_full[b], 1);
             mbar_init(&h.op_empty[b], 1);
+        }
+        for (int b = 0; b < C::DBUF; ++b) {
             mbar_init(&h.d_full[b], 2);          // MMA completion + the issuer's scale hand-off
             mbar_init(&h.d_free[b], NEPI / 32);
         }
@@ -201,7 +226,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     {
-        // T_b hi/lo: [kc][n][8 halves], n = (slot c, j), entry kk = kc*8 + e
+        // T_b hi/lo, K-major [kc][n][8 halves] with n = (slot c, j) and entry kk = kc*8 + e.
+        // CAT: one matrix per b with 2N rows per kc chunk (rows [0,N) hi, [N,2N) lo);
+        // otherwise the hi matrix followed by the lo matrix.
         const float sw = pow2f(p.wexp);
         __half* B = reinterpret_cast<__half*>(smem + C::OFF_B);
         const int per_b = 2 * N * 8;
@@ -214,8 +241,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (c < K && a >= 0 && a < K) v = W.w[(c * K + b) * K + a] * sw;
             const __half hi = __float2half_rn(v);
             const __half lo = __float2half_rn(v - __half2float(hi));
-            B[(2 * b + 0) * (C::B_BYTES / 2) + rem] = hi;
-            B[(2 * b + 1) * (C::B_BYTES / 2) + rem] = lo;
+            if (C::CAT) {
+                __half* Bb = B + b * 2 * (C::B_BYTES / 2);
+                Bb[(kc * 2 * N + n) * 8 + e] = hi;
+                Bb[(kc * 2 * N + N + n) * 8 + e] = lo;
+            } else {
+                B[(2 * b + 0) * (C::B_BYTES / 2) + rem] = hi;
+                B[(2 * b + 1) * (C::B_BYTES / 2) + rem] = lo;
+            }
         }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -258,6 +291,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             // idesc: D f32, A f16, B f16, both K-major, N >> 3 at bit 17, M >> 4 at bit 24
             const uint32_t idesc = (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) |
                                    (static_cast<uint32_t>(MROWS >> 4) << 24);
+            const uint32_t idesc2 = (1u << 4) | (static_cast<uint32_t>((2 * N) >> 3) << 17) |
+                                    (static_cast<uint32_t>(MROWS >> 4) << 24);
             uint32_t g = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < p.nitems && ok; item += gridDim.x) {
@@ -265,10 +300,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int zc0 = zi * p.zchunk, zc1 = min(zc0 + p.zchunk, p.nz);
                 const int nplanes = zc1 - zc0 + 2 * R;
                 for (int it = 0; it < nplanes; ++it, ++g) {
-                    const int ob = g & 1, db = g & 1;
+                    const int ob = g & 1, db = g % C::DBUF;
                     if (!wait_or_abort(&h.op_full[ob], (g >> 1) & 1, abort_flag, p.status) ||
-                        (g >= 2 && !wait_or_abort(&h.d_free[db], ((g >> 1) - 1) & 1, abort_flag,
-                                                  p.status))) {
+                        (g >= C::DBUF && !wait_or_abort(&h.d_free[db], ((g / C::DBUF) - 1) & 1,
+                                                        abort_flag, p.status))) {
                         ok = false;
                         break;
                     }
@@ -277,18 +312,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t op_lo = sbase + C::OFF_OP + (2 * ob + 1) * C::OP_BYTES;
 #pragma unroll
                     for (int t = 0; t < XT; ++t) {
-                        const uint32_t dt = tbase + static_cast<uint32_t>((db * XT + t) * N);
+                        const uint32_t dt = tbase + static_cast<uint32_t>((db * XT + t) * C::DN);
 #pragma unroll
                         for (int b = 0; b < K; ++b) {
                             const uint32_t aoff = t * (ROWS * 16) + b * 16;
                             const uint64_t ahi = umma_desc(op_hi + aoff, ROWS * 16, 128);
                             const uint64_t alo = umma_desc(op_lo + aoff, ROWS * 16, 128);
                             const uint32_t bb = sbase + C::OFF_B + 2 * b * C::B_BYTES;
-                            const uint64_t bhi = umma_desc(bb, N * 16, 128);
-                            const uint64_t blo = umma_desc(bb + C::B_BYTES, N * 16, 128);
-                            umma_f16(dt, ahi, bhi, idesc, b > 0 ? 1u : 0u);
-                            umma_f16(dt, ahi, blo, idesc, 1u);
-                            umma_f16(dt, alo, bhi, idesc, 1u);
+                            if (C::CAT) {
+                                // [T_hi | T_lo] (2N rows per kc chunk); its first N rows are T_hi
+                                const uint64_t bcat = umma_desc(bb, 2 * N * 16, 128);
+                                umma_f16(dt, ahi, bcat, idesc2, b > 0 ? 1u : 0u);
+                                umma_f16(dt, alo, bcat, idesc, 1u);
+                            } else {
+                                const uint64_t bhi = umma_desc(bb, N * 16, 128);
+                                const uint64_t blo = umma_desc(bb + C::B_BYTES, N * 16, 128);
+                                umma_f16(dt, ahi, bhi, idesc, b > 0 ? 1u : 0u);
+                                umma_f16(dt, ahi, blo, idesc, 1u);
+                                umma_f16(dt, alo, bhi, idesc, 1u);
+                            }
                         }
                     }
                     umma_commit(&h.op_empty[ob]);
@@ -419,9 +461,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int j = 0; j < 8; ++j) acc[c][j] = 0.f;
 
             auto plane = [&](const int it, const int u) {
-                const int db = g & 1;
+                const int db = g % C::DBUF;
                 int w = 1;
-                if (lane == 0) w = wait_or_abort(&h.d_full[db], (g >> 1) & 1, abort_flag, p.status) ? 1 : 0;
+                if (lane == 0) w = wait_or_abort(&h.d_full[db], (g / C::DBUF) & 1, abort_flag, p.status) ? 1 : 0;
                 w = __shfl_sync(0xffffffffu, w, 0);
                 if (!w) {
                     ok = false;
@@ -429,15 +471,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const float inv = pow2f(-(h.dsc[db] + p.wexp));
-                const uint32_t col = tbase + lane_addr + static_cast<uint32_t>((db * XT + t) * N);
+                const uint32_t col = tbase + lane_addr + static_cast<uint32_t>((db * XT + t) * C::DN);
+                // two 16-column loads in flight per wait: slots 4q .. 4q+3
 #pragma unroll
-                for (int q = 0; q < N / 16; ++q) {
-                    float d[16];
-                    tmem_ld16(col + q * 16, d);
+                for (int q = 0; q < (N / 16 + 1) / 2; ++q) {
+                    float d[32];
+                    const bool two = 2 * q + 1 < N / 16;
+                    tmem_ld16_nowait(col + 32 * q, d);
+                    if (two) tmem_ld16_nowait(col + 32 * q + 16, d + 16);
+                    tmem_wait_ld();
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int c = 2 * q + h2;
-                        if (c < K) {
+                    for (int h2 = 0; h2 < 4; ++h2) {
+                        const int c = 4 * q + h2;
+                        if (c < K && (h2 < 2 || two)) {
                             const int sl = ((u - c + R) % K + K) % K;
 #pragma unroll
                             for (int j = 0; j < 8; ++j) acc[sl][j] = fmaf(d[8 * h2 + j], inv, acc[sl][j]);

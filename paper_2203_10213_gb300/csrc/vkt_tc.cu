@@ -61,8 +61,11 @@ struct TcCfg {
     static constexpr int STAGE_TX = ROWS * NCH * 8 * 4;
     static constexpr int OP_BYTES = ((NCH * ROWS * 16) + 1023) & ~1023;   // one fp16 plane
     static constexpr int B_BYTES = 2 * N * 16;                            // one Toeplitz (hi or lo)
-    static constexpr int UNITS = NCH * ROWS;                              // (chunk,row) units
-    static constexpr int UPT = (UNITS + NCONV - 1) / NCONV;               // units per thread
+    // converter items: (chunk, row, half) with the half fastest, 4 values each, so that a
+    // quarter warp's 16-byte reads of the stage (rows 96 bytes apart) and its 8-byte writes
+    // of the operand planes touch distinct banks
+    static constexpr int UNITS = NCH * ROWS * 2;
+    static constexpr int UPT = (UNITS + NCONV - 1) / NCONV;               // items per thread
     // shared memory map
     static constexpr int OFF_STAGE = 1024;
     static constexpr int OFF_OP = OFF_STAGE + STAGES * STAGE_BYTES;       // [2 bufs][hi,lo]
@@ -169,13 +172,28 @@ __device__ __forceinline__ void named_sync(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Bounded wait that also gives up when another role has aborted.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait that also gives up when another role has aborted.  The waiting thread asks
+// to be suspended (up to the hint) instead of polling, so idle roles do not take issue
+// slots from the MMA-issuing warp on their sub-partition.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                               unsigned* status)
 {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_sleep(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity)) {
         if (*abort_flag) return false;
         if (global_ns() - t0 > WAIT_LIMIT_NS) {
             *abort_flag = 1;
@@ -293,6 +311,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                    (static_cast<uint32_t>(MROWS >> 4) << 24);
             const uint32_t idesc2 = (1u << 4) | (static_cast<uint32_t>((2 * N) >> 3) << 17) |
                                     (static_cast<uint32_t>(MROWS >> 4) << 24);
+            // Descriptors are built once: B per (dy, part) for the whole kernel, A as a per-
+            // buffer base to which each MMA adds its compile-time offset in the 14-bit start
+            // address field (addresses stay below 256 KB, so the add never carries out), so
+            // the issuing thread spends about one instruction per MMA.
+            uint64_t bdesc[2 * K];
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+                const uint32_t bb = sbase + C::OFF_B + 2 * b * C::B_BYTES;
+                if (C::CAT) {
+                    bdesc[2 * b] = umma_desc(bb, 2 * N * 16, 128);
+                    bdesc[2 * b + 1] = bdesc[2 * b];
+                } else {
+                    bdesc[2 * b] = umma_desc(bb, N * 16, 128);
+                    bdesc[2 * b + 1] = umma_desc(bb + C::B_BYTES, N * 16, 128);
+                }
+            }
+            uint64_t abase[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) abase[q] = umma_desc(sbase + C::OFF_OP + q * C::OP_BYTES, ROWS * 16, 128);
             uint32_t g = 0;
             bool ok = true;
             for (int item = blockIdx.x; item < p.nitems && ok; item += gridDim.x) {
@@ -308,28 +345,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t op_hi = sbase + C::OFF_OP + (2 * ob + 0) * C::OP_BYTES;
-                    const uint32_t op_lo = sbase + C::OFF_OP + (2 * ob + 1) * C::OP_BYTES;
+                    const uint64_t ahi0 = ob ? abase[2] : abase[0];
+                    const uint64_t alo0 = ob ? abase[3] : abase[1];
+                    const uint32_t d0 = tbase + static_cast<uint32_t>(db * XT * C::DN);
 #pragma unroll
                     for (int t = 0; t < XT; ++t) {
-                        const uint32_t dt = tbase + static_cast<uint32_t>((db * XT + t) * C::DN);
+                        const uint32_t dt = d0 + static_cast<uint32_t>(t * C::DN);
 #pragma unroll
                         for (int b = 0; b < K; ++b) {
-                            const uint32_t aoff = t * (ROWS * 16) + b * 16;
-                            const uint64_t ahi = umma_desc(op_hi + aoff, ROWS * 16, 128);
-                            const uint64_t alo = umma_desc(op_lo + aoff, ROWS * 16, 128);
-                            const uint32_t bb = sbase + C::OFF_B + 2 * b * C::B_BYTES;
+                            const uint64_t aoff = static_cast<uint64_t>((t * (ROWS * 16) + b * 16) >> 4);
                             if (C::CAT) {
-                                // [T_hi | T_lo] (2N rows per kc chunk); its first N rows are T_hi
-                                const uint64_t bcat = umma_desc(bb, 2 * N * 16, 128);
-                                umma_f16(dt, ahi, bcat, idesc2, b > 0 ? 1u : 0u);
-                                umma_f16(dt, alo, bcat, idesc, 1u);
+                                umma_f16(dt, ahi0 + aoff, bdesc[2 * b], idesc2, b > 0 ? 1u : 0u);
+                                umma_f16(dt, alo0 + aoff, bdesc[2 * b], idesc, 1u);
                             } else {
-                                const uint64_t bhi = umma_desc(bb, N * 16, 128);
-                                const uint64_t blo = umma_desc(bb + C::B_BYTES, N * 16, 128);
-                                umma_f16(dt, ahi, bhi, idesc, b > 0 ? 1u : 0u);
-                                umma_f16(dt, ahi, blo, idesc, 1u);
-                                umma_f16(dt, alo, bhi, idesc, 1u);
+                                umma_f16(dt, ahi0 + aoff, bdesc[2 * b], idesc, b > 0 ? 1u : 0u);
+                                umma_f16(dt, ahi0 + aoff, bdesc[2 * b + 1], idesc, 1u);
+                                umma_f16(dt, alo0 + aoff, bdesc[2 * b], idesc, 1u);
                             }
                         }
                     }
@@ -369,28 +400,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 const float* st = reinterpret_cast<const float*>(smem + C::OFF_STAGE + s * C::STAGE_BYTES);
-                float v[C::UPT][8];
+                float v[C::UPT][4];
                 float mx = 0.f;
 #pragma unroll
                 for (int q = 0; q < C::UPT; ++q) {
                     const int u = ct + q * NCONV;
                     if (u < C::UNITS) {
-                        const int ch = u / ROWS, row = u - ch * ROWS;
+                        const int hf = u & 1, cr = u >> 1;
+                        const int ch = cr / ROWS, row = cr - ch * ROWS;
                         const int gy = clampi(y0 - R + row, 0, p.ny - 1);
                         const float* sr = st + (gy - (y0 - R)) * (NCH * 8);
-                        const int gx0 = x0 - 4 + 8 * ch;
-                        if (gx0 >= 0 && gx0 + 7 < p.nx) {
-                            const float4 a = *reinterpret_cast<const float4*>(sr + 8 * ch);
-                            const float4 b = *reinterpret_cast<const float4*>(sr + 8 * ch + 4);
+                        const int gx0 = x0 - 4 + 8 * ch + 4 * hf;
+                        if (gx0 >= 0 && gx0 + 3 < p.nx) {
+                            const float4 a = *reinterpret_cast<const float4*>(sr + 8 * ch + 4 * hf);
                             v[q][0] = a.x; v[q][1] = a.y; v[q][2] = a.z; v[q][3] = a.w;
-                            v[q][4] = b.x; v[q][5] = b.y; v[q][6] = b.z; v[q][7] = b.w;
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
+                            for (int e = 0; e < 4; ++e)
                                 v[q][e] = sr[clampi(gx0 + e, 0, p.nx - 1) - (x0 - 4)];
                         }
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) mx = fmaxf(mx, fabsf(v[q][e]));
+                        for (int e = 0; e < 4; ++e) mx = fmaxf(mx, fabsf(v[q][e]));
                     }
                 }
 #pragma unroll
@@ -414,9 +444,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int q = 0; q < C::UPT; ++q) {
                     const int u = ct + q * NCONV;
                     if (u < C::UNITS) {
-                        uint32_t hw[4], lw[4];
+                        uint32_t hw[2], lw[2];
 #pragma unroll
-                        for (int e2 = 0; e2 < 4; ++e2) {
+                        for (int e2 = 0; e2 < 2; ++e2) {
                             const float a = v[q][2 * e2] * sx, b = v[q][2 * e2 + 1] * sx;
                             const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
                             const __half al = __float2half_rn(a - __half2float(ah));
@@ -426,9 +456,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             lw[e2] = static_cast<uint32_t>(__half_as_ushort(al)) |
                                      (static_cast<uint32_t>(__half_as_ushort(bl)) << 16);
                         }
-                        // unit u = (chunk, row) lands at chunk * ROWS*16 + row * 16 = u * 16
-                        *reinterpret_cast<uint4*>(ohi + u * 16) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4*>(olo + u * 16) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        // item u = (chunk, row, half) lands at chunk*ROWS*16 + row*16 + half*8 = u*8
+                        *reinterpret_cast<uint2*>(ohi + u * 8) = make_uint2(hw[0], hw[1]);
+                        *reinterpret_cast<uint2*>(olo + u * 8) = make_uint2(lw[0], lw[1]);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -128,6 +128,21 @@ def test_degenerate_shapes(shape, path, k):
     compare(gpu, ref, w, src, (0, 1), (0, 1), f"{path} k={k} {shape}")
 
 
+def test_smallest_config_uniform64_gaussian3_fp32_path():
+    """64^3 float32, voxels i.i.d. U[0,1) from the seed, normalised 3^3 Gaussian sigma 1.0
+    given as dense weights, FP32 CUDA-core (direct) path, every voxel against the oracle."""
+    src = synth.volume("uniform", synth.F32, (64, 64, 64), synth.BASE_SEED)
+    w = oracle.gaussian_weights(3, 1.0).astype(np.float32)
+    gpu = run_gpu(vkt, src, vkt.Filter.dense(w), torch.float32, path="direct")
+    ref = oracle.correlate(src, w)
+    compare(gpu, ref, w, src, (0, 1), (0, 1), "64^3 uniform gaussian3")
+    # the same filter through the separable path and the automatic choice
+    g = vkt.Filter.gaussian(3, 1.0)
+    for path in ("separable", "auto"):
+        gpu = run_gpu(vkt, src, g, torch.float32, path=path)
+        compare(gpu, ref, w, src, (0, 1), (0, 1), f"64^3 uniform gaussian3 {path}")
+
+
 def test_identity_and_constant_exact():
     shape = (33, 40, 72)
     src = src_volume(synth.F32, shape, SEED + 80)

@@ -172,19 +172,6 @@ __device__ __forceinline__ void named_sync(int id, int n)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded wait that also gives up when another role has aborted.  The waiting thread asks
 // to be suspended (up to the hint) instead of polling, so idle roles do not take issue
 // slots from the MMA-issuing warp on their sub-partition.

@@ -76,9 +76,21 @@ typedef struct vktFilter_impl* vktFilter;
  *   stream      cudaStream_t to enqueue on (NULL = legacy default stream)
  *   printTimes  nonzero: time each call with CUDA events and print it to stderr
  *               (this synchronises the stream after the call)
- *   debug       nonzero: print path choices and launch shapes to stderr
+ *   debug       bit set of VKT_DEBUG_* flags (below)
  *   path        a vktFilterPath forcing the evaluation path (VKT_PATH_AUTO = choose)
  */
+/* print path choices and launch shapes to stderr */
+#define VKT_DEBUG_LOG 1
+/*
+ * Fault injection for tests of failure detection: every CTA of the direct path withholds
+ * the TMA load of its first input plane, so its bounded wait for that plane runs out
+ * (after 2 s).  The CTA then records the timeout in the device status word, waits for the
+ * loads it did issue and exits without writing; the next vktSynchronize returns
+ * VKT_ERROR_DEVICE_TIMEOUT and the context stays usable.  No other path reads this flag,
+ * and calls whose source cannot use a tensor map (rows not 16-byte aligned) ignore it.
+ */
+#define VKT_DEBUG_INJECT_WAIT_TIMEOUT 2
+
 typedef struct vktExecutionPolicy {
     void* stream;
     int32_t printTimes;

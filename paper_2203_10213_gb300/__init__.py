@@ -74,18 +74,28 @@ def get_policy() -> ExecutionPolicy:
     return pol
 
 
-def set_policy(stream=None, path="auto", debug=False, print_times=False) -> None:
-    pol = ExecutionPolicy()
+DEBUG_LOG = 1
+DEBUG_INJECT_WAIT_TIMEOUT = 2
+
+
+def set_policy(stream=None, path=None, debug=None, print_times=None) -> None:
+    """Sets the calling thread's policy.  stream None: torch's current stream; path, debug,
+    print_times None: keep the current setting.  debug: True for DEBUG_LOG, or an int of
+    DEBUG_* bits."""
+    pol = get_policy()
     pol.stream = ctypes.c_void_p(_stream_handle(stream))
-    pol.path = PATHS[path] if isinstance(path, str) else int(path)
-    pol.debug = int(bool(debug))
-    pol.printTimes = int(bool(print_times))
+    if path is not None:
+        pol.path = PATHS[path] if isinstance(path, str) else int(path)
+    if debug is not None:
+        pol.debug = int(debug)
+    if print_times is not None:
+        pol.printTimes = int(bool(print_times))
     check(_lib.vktSetThreadExecutionPolicy(pol))
 
 
 @contextlib.contextmanager
-def policy(stream=None, path="auto", debug=False, print_times=False):
-    """Temporarily sets the calling thread's execution policy."""
+def policy(stream=None, path=None, debug=None, print_times=None):
+    """Temporarily sets the calling thread's execution policy (None: keep the setting)."""
     old = get_policy()
     set_policy(stream, path, debug, print_times)
     try:
@@ -298,9 +308,10 @@ class Filter:
 
 # ------------------------------------------------------------------ ApplyFilter
 
-def apply_filter(dst: StructuredVolume, src: StructuredVolume, filt: Filter, path="auto",
+def apply_filter(dst: StructuredVolume, src: StructuredVolume, filt: Filter, path=None,
                  stream=None) -> None:
-    """Enqueues dst = filter(src) on `stream` (default: torch's current stream)."""
+    """Enqueues dst = filter(src) on `stream` (default: torch's current stream); path None
+    keeps the thread policy's path."""
     with policy(stream=stream, path=path):
         check(_lib.vktApplyFilterSV(dst.handle, src.handle, filt.handle), "vktApplyFilterSV")
 
@@ -328,7 +339,7 @@ def apply_filter_backward(grad_src, grad_weights, grad_dst: StructuredVolume,
 
 
 def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
-                  dst_range=(0.0, 1.0), path="auto", out=None):
+                  dst_range=(0.0, 1.0), path=None, out=None):
     """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor."""
     torch = _torch()
     if out is None:

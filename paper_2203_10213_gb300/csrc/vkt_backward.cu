@@ -229,7 +229,7 @@ vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, floa
     cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
-    if (ctx.debug)
+    if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] wgrad k=%d grid=(%d,%d,%d) zchunk=%d tma=%d\n", K, g.tiles_x * K,
                 g.tiles_y, g.chunks, g.zchunk, a.use_tma);
     k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, ctx.stream>>>(map, a);

@@ -351,7 +351,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     e = cudaGraphInstantiate(&P.exec, graph, 0);
     if (e != cudaSuccess) return from_cuda(e);
     P.kernels = kernels;
-    if (ctx.debug)
+    if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] batch plan: %zu separable volumes, %d + %d compensated bricks, "
                 "grids %d / %d, %zu single launches\n", P.jobs.size(), nfast, ncomp, grid_fast,
                 grid_comp, dense_idx.size());

@@ -8,7 +8,12 @@
 // an input plane is read from shared memory once per thread window and never again.
 //   K <= 3 : the K accumulator planes rotate by unrolling the plane loop K times;
 //   K >= 5 : they rotate by shifting once per plane (less code for the same arithmetic).
-// Weights travel as kernel parameters and enter the FMAs as constant-bank operands.
+// Weights travel as kernel parameters and enter the FMAs as constant-bank operands.  For
+// k = 3 the kernel is bound by instruction issue, not by HBM, so there the x taps of each
+// output pair (x, x+1) run as one packed two-lane FMA (half the FMA instructions), and a
+// thread holds 4 rows instead of 2 so the per-plane overhead spreads over 16 outputs.  A
+// slot's first tap in a plane of its z-march (c = b = a = 0) is a plain product, so no
+// accumulator is ever reset.
 //
 // Adjoint mode (ADJ): the same machinery evaluates dL/dx of the clamped correlation.  With
 // the extension E (x_ext(j) = x(clamp(j)) on the domain padded by r), the forward filter is
@@ -45,6 +50,7 @@ struct DirectArgs {
     int sfmt, dfmt;
     int zchunk;
     int use_tma;
+    int withhold_first;    // fault injection: the first plane's TMA load is never issued
     float a0, a1, qmax;
     unsigned* status;
 };
@@ -52,8 +58,11 @@ struct DirectArgs {
 template <int K>
 struct DirectCfg {
     static constexpr int RX = (K == 9) ? 2 : 4;
-    static constexpr int RY = 2;
+    static constexpr int RY = (K <= 3) ? 4 : 2;
     static constexpr bool ROT = K >= 5;
+    // PAIR: the x taps run as packed two-lane FMAs over neighbouring outputs (x, x+1),
+    // which halves the FMA instructions of a kernel whose time is instruction issue
+    static constexpr bool PAIR = K == 3;
     static constexpr int TX = BX * RX, TY = BY * RY;
     using Geo = Brick<K, TX, TY>;
 };
@@ -122,9 +131,10 @@ __global__ void __launch_bounds__(NT)
         if (p.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
-    int issued = 0;   // TMA loads issued so far (thread 0 only)
+    int issued = 0;   // planes handed to the TMA unit so far (thread 0 only)
     if (p.use_tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+            if (s == 0 && p.withhold_first) continue;
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
                         ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1));
@@ -134,13 +144,20 @@ __global__ void __launch_bounds__(NT)
     ConvPlan<Geo, NT, !ADJ> plan;
     plan.init(sfmt, p.nx, p.ny, x0, y0, tid);
 
-    float acc[K][RY][RX];
+    // Accumulators start at zero once; afterwards the first tap a plane's slot receives
+    // (c = 0, b = 0, a = 0) is a plain product, which restarts the slot without a reset.
+    // outputs (x, x+1) of a row share one float2, the operand of the packed FMAs
+    static_assert(RX % 2 == 0, "outputs are paired along x");
+    float2 acc[K][RY][RX / 2];
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
         for (int i = 0; i < RY; ++i)
 #pragma unroll
-            for (int x = 0; x < RX; ++x) acc[s][i][x] = 0.f;
+            for (int x = 0; x < RX / 2; ++x) acc[s][i][x] = make_float2(0.f, 0.f);
+    auto lane = [&](int s, int i, int x) -> float& {
+        return (x & 1) ? acc[s][i][x >> 1].y : acc[s][i][x >> 1].x;
+    };
 
     const int ox = x0 + tx * RX;
     const int nvalid = p.nx - ox;
@@ -182,11 +199,29 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                 for (int c = 0; c < K; ++c) {
                     const int sl = Cfg::ROT ? (K - 1 - c) : (((u - c + R) % K + K) % K);
+                    if constexpr (Cfg::PAIR) {
 #pragma unroll
-                    for (int x = 0; x < RX; ++x)
+                        for (int x = 0; x < RX; x += 2)
 #pragma unroll
-                        for (int a = 0; a < K; ++a)
-                            acc[sl][i][x] = fmaf(W.w[(c * K + b) * K + a], win[x + a], acc[sl][i][x]);
+                            for (int a = 0; a < K; ++a) {
+                                const float wv = W.w[(c * K + b) * K + a];
+                                const float2 w2 = make_float2(wv, wv);
+                                const float2 v2 = make_float2(win[x + a], win[x + a + 1]);
+                                float2& d = acc[sl][i][x >> 1];
+                                d = (c == 0 && b == 0 && a == 0) ? __fmul2_rn(w2, v2)
+                                                                 : __ffma2_rn(w2, v2, d);
+                            }
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < RX; ++x)
+#pragma unroll
+                            for (int a = 0; a < K; ++a) {
+                                const float wv = W.w[(c * K + b) * K + a];
+                                float& d = lane(sl, i, x);
+                                d = (c == 0 && b == 0 && a == 0) ? wv * win[x + a]
+                                                                 : fmaf(wv, win[x + a], d);
+                            }
+                    }
                 }
             }
         }
@@ -197,12 +232,15 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const int oy = y0 + ty * RY + i;
+                float row[RX];
+#pragma unroll
+                for (int x = 0; x < RX; ++x) row[x] = lane(sl0, i, x);
                 if (ADJ) {
                     store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
-                                          ox, acc[sl0][i]);
+                                          ox, row);
                 } else if (oy < p.ny && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
-                    store_row<RX>(p.dst, dfmt, idx, nvalid, acc[sl0][i], p.a0, p.a1, p.qmax);
+                    store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax);
                 }
             }
         }
@@ -212,16 +250,7 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                 for (int i = 0; i < RY; ++i)
 #pragma unroll
-                    for (int x = 0; x < RX; ++x) acc[q][i][x] = acc[q + 1][i][x];
-#pragma unroll
-            for (int i = 0; i < RY; ++i)
-#pragma unroll
-                for (int x = 0; x < RX; ++x) acc[K - 1][i][x] = 0.f;
-        } else {
-#pragma unroll
-            for (int i = 0; i < RY; ++i)
-#pragma unroll
-                for (int x = 0; x < RX; ++x) acc[sl0][i][x] = 0.f;
+                    for (int x = 0; x < RX / 2; ++x) acc[q][i][x] = acc[q + 1][i][x];
         }
     };
 
@@ -244,7 +273,7 @@ __global__ void __launch_bounds__(NT)
             // drain loads still in flight (bounded) before the CTA's smem is released:
             // the newest load issued to each stage completes that stage's current phase
             for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
-                mbar_wait(&bars[it % STAGES], (it / STAGES) & 1);
+                if (it != 0 || !p.withhold_first) mbar_wait(&bars[it % STAGES], (it / STAGES) & 1);
         }
         __syncthreads();
     }
@@ -268,6 +297,7 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     a.a1 = job.a1;
     a.qmax = job.qmax;
     a.status = ctx.status;
+    a.withhold_first = (ctx.debug & VKT_DEBUG_INJECT_WAIT_TIMEOUT) ? 1 : 0;
     if (ADJ) {
         // padded output domain [-r, n+r) per axis; x starts 16 bytes left of the domain
         // so that every tile's TMA box starts on a 16-byte boundary
@@ -320,9 +350,9 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
-    if (ctx.debug)
-        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
-                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma);
+    if (ctx.debug & VKT_DEBUG_LOG)
+        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d withhold=%d\n",
+                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma, a.withhold_first);
     kern<<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
     count_launches(1);
     return from_cuda(cudaGetLastError());

@@ -106,7 +106,7 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
-    if (ctx.debug)
+    if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] separable%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
                 J.comp ? "-compensated" : "", K, J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem,
                 J.use_tma);

@@ -587,7 +587,7 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     cudaError_t e = cudaFuncSetAttribute(k_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return from_cuda(e);
     const int grid = static_cast<int>(std::min<long>(a.nitems, sms));
-    if (ctx.debug)
+    if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] tensor k=%d items=%d (%dx%dx%d, zchunk %d) grid=%d smem=%d\n", K,
                 a.nitems, a.items_x, a.items_y, a.items_z, a.zchunk, grid, C::SMEM);
     k_tc<K><<<grid, NTHREADS, C::SMEM, ctx.stream>>>(map, a, W);

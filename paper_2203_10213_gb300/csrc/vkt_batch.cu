@@ -215,6 +215,9 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
                                          raw_width(J.k, J.sfmt), ty + 2 * ((J.k - 1) / 2), 1)
                         ? 1
                         : 0;
+        // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
+        // per row, when the volume starts on a 16-byte boundary
+        J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
         smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0));
         order.push_back({-static_cast<long>(J.k) * (J.zchunk + J.k - 1), static_cast<int>(j)});
     }

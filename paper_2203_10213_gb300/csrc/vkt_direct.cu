@@ -50,6 +50,7 @@ struct DirectArgs {
     int sfmt, dfmt;
     int zchunk;
     int use_tma;
+    int rows;              // no tensor map: stages filled by per-row bulk copies (forward only)
     int withhold_first;    // fault injection: the first plane's TMA load is never issued
     float a0, a1, qmax;
     unsigned* status;
@@ -132,6 +133,8 @@ __global__ void __launch_bounds__(NT)
     }
     __syncthreads();
     int issued = 0;   // planes handed to the TMA unit so far (thread 0 only)
+    const bool rows = !ADJ && p.rows;
+    const uint64_t vol_bytes = static_cast<uint64_t>(p.nx) * p.ny * p.nz * fmt_bytes(sfmt);
     if (p.use_tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             if (s == 0 && p.withhold_first) continue;
@@ -139,10 +142,19 @@ __global__ void __launch_bounds__(NT)
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
                         ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1));
         }
+    } else if (rows) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s)
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
+                                p.nz, x0, y0, pfirst + s, tid);
+        __syncthreads();   // every thread's expect_tx precedes the single arrival
+        if (tid == 0)
+            for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[s]);
     }
+    // row copies issued in one plane get their arrival after the next plane's CTA barrier
+    int pend = -1;
 
     ConvPlan<Geo, NT, !ADJ> plan;
-    plan.init(sfmt, p.nx, p.ny, x0, y0, tid);
+    plan.init(sfmt, p.nx, p.ny, x0, y0, tid, rows);
 
     // Accumulators start at zero once; afterwards the first tap a plane's slot receives
     // (c = 0, b = 0, a = 0) is a plain product, which restarts the slot without a reset.
@@ -169,23 +181,45 @@ __global__ void __launch_bounds__(NT)
         const unsigned char* rs = raw + s * rawb;
         float* Fb = F + (it & 1) * FH * FP;
         bool ok = true;
-        if (p.use_tma) {
+        if (p.use_tma || rows) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, sfmt, p.nx,
                                           p.ny, p.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
-        if (ok) plan.convert(rs, sfmt, Fb, tid);
+        if (ok) {
+            if constexpr (!ADJ) {
+                if (rows) {
+                    const uint32_t zterm =
+                        static_cast<uint32_t>(clampi(pfirst + it, 0, p.nz - 1)) *
+                        static_cast<uint32_t>(p.ny) * static_cast<uint32_t>(p.nx);
+                    plan.convert_rows(rs, sfmt, Fb, tid, p.nx, p.ny, x0, y0, zterm);
+                } else {
+                    plan.convert(rs, sfmt, Fb, tid);
+                }
+            } else {
+                plan.convert(rs, sfmt, Fb, tid);
+            }
+        }
         if (__syncthreads_or(!ok)) {
             failed = true;
             return;
         }
+        if (rows && tid == 0 && pend >= 0) {
+            mbar_arrive(&bars[pend]);
+            ++issued;
+        }
+        pend = -1;
         if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
                         ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1));
             ++issued;
+        } else if (rows && it + STAGES < nplanes) {
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
+                                p.nz, x0, y0, pfirst + it + STAGES, tid);
+            pend = s;
         }
         // multiply the plane into the accumulators
 #pragma unroll
@@ -270,6 +304,11 @@ __global__ void __launch_bounds__(NT)
     if (failed) {
         if (tid == 0) {
             atomicOr(p.status, STATUS_TIMEOUT);
+            // a refill whose copies are in flight still needs its arrival before the drain
+            if (pend >= 0) {
+                mbar_arrive(&bars[pend]);
+                ++issued;
+            }
             // drain loads still in flight (bounded) before the CTA's smem is released:
             // the newest load issued to each stage completes that stage's current phase
             for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
@@ -339,6 +378,10 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
                     ? 1
                     : 0;
     if (!a.use_tma) memset(&map, 0, sizeof(map));
+    // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
+    // per row, when the volume starts on a 16-byte boundary (forward only: the adjoint
+    // needs the zero extension a tensor map or the plain loads give)
+    a.rows = (!ADJ && !a.use_tma && reinterpret_cast<uintptr_t>(job.src) % 16 == 0) ? 1 : 0;
 
     const size_t smem = direct_smem_bytes<K>(job.sfmt);
     // the common float32 destinations get kernels with their formats compiled in
@@ -351,8 +394,9 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
     if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d withhold=%d\n",
-                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma, a.withhold_first);
+        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d withhold=%d\n",
+                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma, a.rows,
+                a.withhold_first);
     kern<<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
     count_launches(1);
     return from_cuda(cudaGetLastError());

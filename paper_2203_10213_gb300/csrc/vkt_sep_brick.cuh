@@ -23,6 +23,11 @@ constexpr int BX = 16, BY = 16;
 constexpr int RX = 4, RY = 2;
 constexpr int TX = BX * RX, TY = BY * RY;
 constexpr int STAGES = 4;
+// the y and z passes run as packed two-lane FMAs over output pairs (x, x+1) for k <= 5 (at
+// k >= 7, and in the run-time-format kernels at k = 5, the register pairs cost spills or
+// more than the halved FMA issue saves); SF: the compile-time source format or -1
+template <int K, int SF>
+constexpr bool pair_yz() { return K <= 3 || (K == 5 && SF >= 0); }
 
 // Everything a brick needs about its volume (the batched kernel reads these from a table).
 struct Job {
@@ -32,6 +37,7 @@ struct Job {
     int sfmt, dfmt;
     int zchunk;
     int use_tma;
+    int rows;          // no tensor map: stages filled by per-row bulk copies (issue_rows)
     int k;
     int tiles_x, tiles_y, chunks;
     float a0, a1, qmax;
@@ -99,6 +105,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const uint32_t g0 = gplane;
 
     int issued = 0;
+    const uint64_t vol_bytes =
+        static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(sfmt);
     if (J.use_tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
@@ -106,18 +114,39 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
+    } else if (J.rows) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s) {
+            const uint32_t q = g0 + s;
+            issue_rows<Geo, NT>(raw + (q % STAGES) * rawb, &bars[q % STAGES], J.src, vol_bytes,
+                                sfmt, J.nx, J.ny, J.nz, x0, y0, pfirst + s, tid);
+        }
+        __syncthreads();   // every thread's expect_tx precedes the single arrival
+        if (tid == 0)
+            for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % STAGES]);
     }
 
     ConvPlan<Geo, NT> plan;
-    plan.init(sfmt, J.nx, J.ny, x0, y0, tid);
+    plan.init(sfmt, J.nx, J.ny, x0, y0, tid, J.rows != 0);
 
-    float acc[K][RY][RX];
+    // accumulators of the K output planes.  Packed kernels pair outputs (x, x+1) in one
+    // float2, start at zero once, and afterwards give a slot's first tap in its z-march
+    // (c = 0) as a plain product, so a retired slot needs no reset; the others keep scalar
+    // accumulators that are reset after each store (fewer register-pair constraints)
+    constexpr bool PAIR = pair_yz<K, SF>();
+    float2 acc2[PAIR ? K : 1][RY][RX / 2];
+    float acc[PAIR ? 1 : K][RY][RX];
 #pragma unroll
     for (int s = 0; s < K; ++s)
 #pragma unroll
         for (int i = 0; i < RY; ++i)
 #pragma unroll
-            for (int x = 0; x < RX; ++x) acc[s][i][x] = 0.f;
+            for (int x = 0; x < RX; ++x) {
+                if constexpr (PAIR) {
+                    if (x % 2 == 0) acc2[s][i][x / 2] = make_float2(0.f, 0.f);
+                } else {
+                    acc[s][i][x] = 0.f;
+                }
+            }
 
     const int ox = x0 + tx * RX;
     const int nvalid = J.nx - ox;
@@ -128,14 +157,22 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
-        if (J.use_tma) {
+        if (J.use_tma || J.rows) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, sfmt, J.nx, J.ny,
                                     J.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
-        if (ok) plan.convert(rs, sfmt, F, tid);
+        if (ok) {
+            if (J.rows) {
+                const uint32_t zterm = static_cast<uint32_t>(clampi(pfirst + it, 0, J.nz - 1)) *
+                                       static_cast<uint32_t>(J.ny) * static_cast<uint32_t>(J.nx);
+                plan.convert_rows(rs, sfmt, F, tid, J.nx, J.ny, x0, y0, zterm);
+            } else {
+                plan.convert(rs, sfmt, F, tid);
+            }
+        }
         if (__syncthreads_or(!ok)) {
             failed = true;
             return;
@@ -145,6 +182,10 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
                         clampi(pfirst + it + STAGES, 0, J.nz - 1));
             ++issued;
+        } else if (J.rows && it + STAGES < nplanes) {
+            // all threads; the arrival follows the x-pass barrier below
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, sfmt, J.nx, J.ny,
+                                J.nz, x0, y0, pfirst + it + STAGES, tid);
         }
         // x pass: T1[row][x] = sum_a gx[a] F[row][x + a], 4 outputs per item
 #pragma unroll
@@ -167,48 +208,96 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             }
         }
         __syncthreads();
+        // the stage refilled by row copies above is complete in expectation: one arrival
+        if (J.rows && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive(&bars[s]);
+            ++issued;
+        }
         // y pass into registers, then the z pass into the K rotating accumulator planes
-        float t2[RY][RX];
+        const int sl0 = ((u - R) % K + K) % K;
+        // stores the completed output plane it - R (once it >= 2R)
+        auto store_plane = [&](const float (&rowv)[RX], int i) {
+            const int oy = y0 + ty * RY + i;
+            if (it >= 2 * R && oy < J.ny && nvalid > 0) {
+                const int64_t idx = (static_cast<int64_t>(pfirst + it - R) * J.ny + oy) * J.nx + ox;
+                store_row<RX>(J.dst, dfmt, idx, nvalid, rowv, J.a0, J.a1, J.qmax);
+            }
+        };
+        if constexpr (PAIR) {
+            float2 t2[RY][RX / 2];   // first tap of a row (b = 0) is a plain product
 #pragma unroll
-        for (int i = 0; i < RY; ++i)
+            for (int j = 0; j < RY + K - 1; ++j) {
+                float v[RX];
+                load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
 #pragma unroll
-            for (int x = 0; x < RX; ++x) t2[i][x] = 0.f;
+                for (int i = 0; i < RY; ++i) {
+                    const int b = j - i;
+                    if (b < 0 || b >= K) continue;
+                    const float2 w2 = make_float2(G.gy[b], G.gy[b]);
 #pragma unroll
-        for (int j = 0; j < RY + K - 1; ++j) {
-            float v[RX];
-            load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
+                    for (int x = 0; x < RX; x += 2) {
+                        const float2 v2 = make_float2(v[x], v[x + 1]);
+                        float2& d = t2[i][x >> 1];
+                        d = (b == 0) ? __fmul2_rn(w2, v2) : __ffma2_rn(w2, v2, d);
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const int sl = ((u - c + R) % K + K) % K;
+                const float2 w2 = make_float2(G.gz[c], G.gz[c]);
+#pragma unroll
+                for (int i = 0; i < RY; ++i)
+#pragma unroll
+                    for (int x = 0; x < RX / 2; ++x) {
+                        float2& d = acc2[sl][i][x];
+                        d = (c == 0) ? __fmul2_rn(w2, t2[i][x]) : __ffma2_rn(w2, t2[i][x], d);
+                    }
+            }
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
-                const int b = j - i;
-                if (b < 0 || b >= K) continue;
+                float rowv[RX];
 #pragma unroll
-                for (int x = 0; x < RX; ++x) t2[i][x] = fmaf(G.gy[b], v[x], t2[i][x]);
+                for (int x = 0; x < RX; x += 2) {
+                    rowv[x] = acc2[sl0][i][x >> 1].x;
+                    rowv[x + 1] = acc2[sl0][i][x >> 1].y;
+                }
+                store_plane(rowv, i);
             }
-        }
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-            const int sl = ((u - c + R) % K + K) % K;
+        } else {
+            float t2[RY][RX];
 #pragma unroll
             for (int i = 0; i < RY; ++i)
 #pragma unroll
-                for (int x = 0; x < RX; ++x) acc[sl][i][x] = fmaf(G.gz[c], t2[i][x], acc[sl][i][x]);
-        }
-        const int sl0 = ((u - R) % K + K) % K;
-        if (it >= 2 * R) {
-            const int oz = pfirst + it - R;
+                for (int x = 0; x < RX; ++x) t2[i][x] = 0.f;
 #pragma unroll
-            for (int i = 0; i < RY; ++i) {
-                const int oy = y0 + ty * RY + i;
-                if (oy < J.ny && nvalid > 0) {
-                    const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
-                    store_row<RX>(J.dst, dfmt, idx, nvalid, acc[sl0][i], J.a0, J.a1, J.qmax);
+            for (int j = 0; j < RY + K - 1; ++j) {
+                float v[RX];
+                load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
+#pragma unroll
+                for (int i = 0; i < RY; ++i) {
+                    const int b = j - i;
+                    if (b < 0 || b >= K) continue;
+#pragma unroll
+                    for (int x = 0; x < RX; ++x) t2[i][x] = fmaf(G.gy[b], v[x], t2[i][x]);
                 }
             }
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                const int sl = ((u - c + R) % K + K) % K;
+#pragma unroll
+                for (int i = 0; i < RY; ++i)
+#pragma unroll
+                    for (int x = 0; x < RX; ++x)
+                        acc[sl][i][x] = fmaf(G.gz[c], t2[i][x], acc[sl][i][x]);
+            }
+#pragma unroll
+            for (int i = 0; i < RY; ++i) store_plane(acc[sl0][i], i);
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int x = 0; x < RX; ++x) acc[sl0][i][x] = 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int x = 0; x < RX; ++x) acc[sl0][i][x] = 0.f;
     };
 
     for (int g = 0; g * K < nplanes && !failed; ++g) {
@@ -219,8 +308,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             plane(it, u);
         }
     }
-    // only TMA bricks move the stage barriers through their phases
-    if (J.use_tma) gplane = g0 + nplanes;
+    // only bricks loaded through the stage barriers move them through their phases
+    if (J.use_tma || J.rows) gplane = g0 + nplanes;
 
     if (failed) {
         if (tid == 0) {
@@ -326,6 +415,8 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
     const uint32_t g0 = gplane;
 
     int issued = 0;
+    const uint64_t vol_bytes =
+        static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(J.sfmt);
     if (J.use_tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
@@ -333,9 +424,18 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
+    } else if (J.rows) {
+        for (int s = 0; s < STAGES && s < nplanes; ++s) {
+            const uint32_t q = g0 + s;
+            issue_rows<Geo, NT>(raw + (q % STAGES) * rawb, &bars[q % STAGES], J.src, vol_bytes,
+                                J.sfmt, J.nx, J.ny, J.nz, x0, y0, pfirst + s, tid);
+        }
+        __syncthreads();   // every thread's expect_tx precedes the single arrival
+        if (tid == 0)
+            for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % STAGES]);
     }
     ConvPlan<Geo, NT> plan;
-    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid);
+    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid, J.rows != 0);
 
     float acc_s[K][RX], acc_c[K][RX];
 #pragma unroll
@@ -353,14 +453,22 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
-        if (J.use_tma) {
+        if (J.use_tma || J.rows) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, J.sfmt, J.nx, J.ny,
                                     J.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
-        if (ok) plan.convert(rs, J.sfmt, F, tid);
+        if (ok) {
+            if (J.rows) {
+                const uint32_t zterm = static_cast<uint32_t>(clampi(pfirst + it, 0, J.nz - 1)) *
+                                       static_cast<uint32_t>(J.ny) * static_cast<uint32_t>(J.nx);
+                plan.convert_rows(rs, J.sfmt, F, tid, J.nx, J.ny, x0, y0, zterm);
+            } else {
+                plan.convert(rs, J.sfmt, F, tid);
+            }
+        }
         if (__syncthreads_or(!ok)) {
             failed = true;
             return;
@@ -370,6 +478,10 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
                         clampi(pfirst + it + STAGES, 0, J.nz - 1));
             ++issued;
+        } else if (J.rows && it + STAGES < nplanes) {
+            // all threads; the arrival follows the x-pass barrier below
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, J.sfmt, J.nx, J.ny,
+                                J.nz, x0, y0, pfirst + it + STAGES, tid);
         }
         // x pass (inputs exact): T1[row][x] = Dot2(gx, F[row][x .. x+k-1])
 #pragma unroll
@@ -389,6 +501,11 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             }
         }
         __syncthreads();
+        // the stage refilled by row copies above is complete in expectation: one arrival
+        if (J.rows && tid == 0 && it + STAGES < nplanes) {
+            mbar_arrive(&bars[s]);
+            ++issued;
+        }
         // y pass on the (hi, lo) pairs, then the z pass into the K rotating pair accumulators
         float ts[RX], tc[RX];
 #pragma unroll
@@ -436,7 +553,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             plane(it, u);
         }
     }
-    if (J.use_tma) gplane = g0 + nplanes;
+    if (J.use_tma || J.rows) gplane = g0 + nplanes;
     if (failed) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);

@@ -10,10 +10,10 @@
 namespace vkt {
 namespace {
 
-// CTAs per SM the register allocation must allow; format-specialised kernels keep more of
-// their plane loop in registers and get two
+// CTAs per SM the register allocation must allow: three where that costs no spills (k = 3,
+// and the run-time-format kernels up to k = 5), else two
 template <int K, int SF>
-constexpr int sep_min_blocks() { return (K <= 5 && SF < 0) ? 3 : 2; }
+constexpr int sep_min_blocks() { return (K <= 3 || (K <= 5 && SF < 0)) ? 3 : 2; }
 
 // SF/DF: source and destination formats fixed at compile time (-1: read from the job)
 template <int K, int SF = -1, int DF = -1>
@@ -91,13 +91,17 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                                      Geo::raw_w(job.sfmt), ty + 2 * Geo::R, 1)
                     ? 1
                     : 0;
+    // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
+    // per row, when the volume starts on a 16-byte boundary
+    J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
     if (!J.use_tma) memset(&map, 0, sizeof(map));
     const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt) : sep::smem_bytes<K>(job.sfmt);
     // the common float32 destinations get kernels with their formats compiled in
     auto fast = k_separable<K>;
     if constexpr (K >= 3 && K <= 7) {
-        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_U8) fast = k_separable<K, FMT_U8, FMT_F32>;
-        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_F32) fast = k_separable<K, FMT_F32, FMT_F32>;
+        if (!J.comp && J.dfmt == FMT_F32 && (J.sfmt == FMT_U8 || J.sfmt == FMT_F32)) {
+            fast = J.sfmt == FMT_U8 ? k_separable<K, FMT_U8, FMT_F32> : k_separable<K, FMT_F32, FMT_F32>;
+        }
     }
     cudaError_t e = J.comp ? cudaFuncSetAttribute(k_separable_comp<K>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -107,9 +111,9 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                                                   static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
     if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] separable%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d\n",
+        fprintf(stderr, "[vkt] separable%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d\n",
                 J.comp ? "-compensated" : "", K, J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem,
-                J.use_tma);
+                J.use_tma, J.rows);
     const dim3 grid(J.tiles_x, J.tiles_y, J.chunks);
     if (J.comp)
         k_separable_comp<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);

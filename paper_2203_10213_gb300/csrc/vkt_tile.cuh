@@ -104,6 +104,18 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// 1-D bulk copy global -> shared (both addresses 16-byte aligned, bytes a multiple of 16)
+// completing `bytes` transactions on the mbarrier
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes,
+                                             uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tensor_map(const CUtensorMap* map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -123,56 +135,132 @@ struct Brick {
     static constexpr int FGROUPS = FP / 4;          // float4 groups per row
     static_assert(R <= 4, "x halo of a float32 raw tile is 4 voxels");
     __host__ __device__ static constexpr int raw_w(int fmt) { return TX + 2 * fmt_xalign(fmt); }
-    // bytes one TMA box delivers, and the (128-byte padded) size of one raw stage
+    // bytes one TMA box delivers
     __host__ __device__ static constexpr int raw_tx(int fmt) { return raw_w(fmt) * FH * fmt_bytes(fmt); }
-    __host__ __device__ static constexpr int raw_bytes(int fmt) { return (raw_tx(fmt) + 127) & ~127; }
+    // row pitch (bytes) of a stage filled by row copies: a raw row plus up to 15 bytes of
+    // 16-byte misalignment in front of it
+    __host__ __device__ static constexpr int row_pitch(int fmt) { return raw_w(fmt) * fmt_bytes(fmt) + 16; }
+    // the (128-byte padded) size of one raw stage, enough for either way of filling it
+    __host__ __device__ static constexpr int raw_bytes(int fmt) { return (FH * row_pitch(fmt) + 127) & ~127; }
 };
 
-__device__ __forceinline__ float load_raw(const unsigned char* raw, int fmt, int idx)
+// Row-copy loading, for volumes whose rows are not a multiple of 16 bytes long (no tensor
+// map can describe them).  Stage row r (r < FH, global row y0 - R + r inside the volume) is
+// filled by one 1-D bulk copy of the 16-byte aligned span around raw columns
+// [0, raw_w) = voxels [x0 - xa, x0 - xa + raw_w) of plane clamp(z); the raw column 0 of the
+// row lands at the row's misalignment (row_shift_elems) in the stage row.  Rows outside the
+// volume are not copied: the clamped conversion never reads them.  The copies are clipped
+// to the volume's full 16-byte blocks, so no byte outside the volume is read; the few bytes
+// of the last partial block a row needs are read with plain loads.
+//
+// Every thread of the CTA calls issue_rows; thread (lane l, warp w) takes row 8 l + w, so
+// the rows spread over the warps.  Each copying thread first adds its bytes to the stage
+// barrier's transaction count (expect_tx, no arrival), then starts its copy.  The caller
+// makes the barrier's single arrival (rows_arrive) from one thread after a CTA barrier that
+// follows every thread's issue_rows, so the phase cannot complete before all bytes are
+// expected, and the plain-loaded bytes are visible to whoever waits on the phase.
+__device__ __forceinline__ uint32_t row_shift_elems(uint32_t zterm, int gy, int nx, int x0, int xa,
+                                                    int fmt)
 {
-    if (fmt == FMT_F32) return reinterpret_cast<const float*>(raw)[idx];
-    if (fmt == FMT_U16) return static_cast<float>(reinterpret_cast<const uint16_t*>(raw)[idx]);
-    return static_cast<float>(raw[idx]);
+    const uint32_t mask = static_cast<uint32_t>(16 / fmt_bytes(fmt)) - 1u;
+    return (zterm + static_cast<uint32_t>(gy) * static_cast<uint32_t>(nx) +
+            static_cast<uint32_t>(x0 - xa)) & mask;
 }
 
-__device__ __forceinline__ float load_global(const void* src, int fmt, int64_t idx)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
-    if (fmt == FMT_F32) return __ldg(reinterpret_cast<const float*>(src) + idx);
-    if (fmt == FMT_U16) return static_cast<float>(__ldg(reinterpret_cast<const uint16_t*>(src) + idx));
-    return static_cast<float>(__ldg(reinterpret_cast<const unsigned char*>(src) + idx));
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+template <typename Geo, int NT>
+__device__ __forceinline__ void issue_rows(unsigned char* stage, uint64_t* bar, const void* src,
+                                           uint64_t vol_bytes, int fmt, int nx, int ny, int nz,
+                                           int x0, int y0, int z, int tid)
+{
+    static_assert(NT % 32 == 0 && Geo::FH <= 32 * (NT / 32), "one row per thread at most");
+    const int r = (tid & 31) * (NT / 32) + (tid >> 5);
+    if (r >= Geo::FH) return;
+    const int yy = y0 - Geo::R + r;
+    if (yy < 0 || yy >= ny) return;
+    const int es = fmt_bytes(fmt);
+    const int xa = fmt_xalign(fmt);
+    const int64_t need = static_cast<int64_t>(Geo::raw_w(fmt)) * es;
+    const int64_t full = static_cast<int64_t>(vol_bytes & ~uint64_t(15));
+    const int gz = clampi(z, 0, nz - 1);
+    const unsigned char* base = static_cast<const unsigned char*>(src);
+    const int64_t b0 = ((static_cast<int64_t>(gz) * ny + yy) * nx + (x0 - xa)) * es;
+    const int64_t a0 = b0 - (b0 & 15);          // floor to 16 bytes (also for b0 < 0)
+    const int64_t a1 = (b0 + need + 15) & ~int64_t(15);
+    const int64_t lo = a0 > 0 ? a0 : 0;
+    const int64_t hi = a1 < full ? a1 : full;
+    unsigned char* row = stage + r * Geo::row_pitch(fmt);
+    if (hi > lo) {
+        mbar_expect_tx(bar, static_cast<uint32_t>(hi - lo));
+        bulk_load_1d(row + (lo - a0), base + lo, static_cast<uint32_t>(hi - lo), bar);
+    }
+    // bytes past the last full block that this row needs
+    const int64_t t1 = (b0 + need) < static_cast<int64_t>(vol_bytes) ? (b0 + need)
+                                                                      : static_cast<int64_t>(vol_bytes);
+    for (int64_t bb = (full > b0 ? full : b0); bb < t1; ++bb) row[bb - a0] = __ldg(base + bb);
 }
 
 // Fills the raw tile of plane z with plain loads (the path for volumes whose rows cannot
-// be described by a tensor map).  CLAMP: positions outside the volume receive the clamped
-// neighbour (the conversion never reads them anyway); otherwise they receive zero, the
-// zero extension the adjoint needs (and what a TMA load writes there).
+// be described by a tensor map).  Only the columns the conversion reads are written: raw
+// columns [xa - R, xa + TX + R), i.e. voxels x0 - R .. x0 + TX + R - 1.  Each warp takes
+// whole rows and its lanes consecutive columns, so the loads of a warp are coalesced and
+// no index needs a division; a lane's loads of one row are issued together before their
+// stores.  CLAMP: positions outside the volume receive the
+// clamped neighbour (the conversion never reads them anyway); otherwise they receive zero,
+// the zero extension the adjoint needs (and what a TMA load writes there).
 template <typename Geo, int NT, bool CLAMP = true>
 __device__ __forceinline__ void fill_raw_plain(unsigned char* raw, const void* src, int fmt,
                                                int nx, int ny, int nz, int x0, int y0, int z,
                                                int tid)
 {
+    constexpr int NW = NT / 32;
+    constexpr int COLS = Geo::FW;
     const int xa = fmt_xalign(fmt);
     const int rw = Geo::raw_w(fmt);
-    const int n = rw * Geo::FH;
+    const int warp = tid >> 5, lane = tid & 31;
     const bool zin = z >= 0 && z < nz;
-    const int zc = clampi(z, 0, nz - 1);
-    const int64_t plane = static_cast<int64_t>(zc) * nx * ny;
-    for (int e = tid; e < n; e += NT) {
-        const int row = e / rw, col = e - row * rw;
-        const int yy = y0 - Geo::R + row, xx = x0 - xa + col;
-        const bool in = zin && yy >= 0 && yy < ny && xx >= 0 && xx < nx;
-        const int gy = clampi(yy, 0, ny - 1);
-        const int gx = clampi(xx, 0, nx - 1);
-        const int64_t gi = plane + static_cast<int64_t>(gy) * nx + gx;
-        if (fmt == FMT_F32) {
-            const float v = __ldg(reinterpret_cast<const float*>(src) + gi);
-            reinterpret_cast<float*>(raw)[e] = (CLAMP || in) ? v : 0.f;
-        } else if (fmt == FMT_U16) {
-            const uint16_t v = __ldg(reinterpret_cast<const uint16_t*>(src) + gi);
-            reinterpret_cast<uint16_t*>(raw)[e] = (CLAMP || in) ? v : 0;
-        } else {
-            const unsigned char v = __ldg(reinterpret_cast<const unsigned char*>(src) + gi);
-            raw[e] = (CLAMP || in) ? v : 0;
+    const int64_t plane = static_cast<int64_t>(clampi(z, 0, nz - 1)) * nx * ny;
+#pragma unroll 1
+    for (int rr = 0; rr < (Geo::FH + NW - 1) / NW; ++rr) {
+        const int row = warp + rr * NW;
+        if (row >= Geo::FH) break;
+        const int yy = y0 - Geo::R + row;
+        const bool yin = zin && yy >= 0 && yy < ny;
+        const int64_t rbase = plane + static_cast<int64_t>(clampi(yy, 0, ny - 1)) * nx;
+        const int dbase = row * rw + xa - Geo::R;
+        // a row's loads first (in flight together), then its shared-memory stores
+        constexpr int NC = (COLS + 31) / 32;
+        uint32_t v[NC];
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            const int c = min(lane + cc * 32, COLS - 1);
+            const int64_t gi = rbase + clampi(x0 - Geo::R + c, 0, nx - 1);
+            if (fmt == FMT_F32)
+                v[cc] = __float_as_uint(__ldg(reinterpret_cast<const float*>(src) + gi));
+            else if (fmt == FMT_U16)
+                v[cc] = __ldg(reinterpret_cast<const uint16_t*>(src) + gi);
+            else
+                v[cc] = __ldg(reinterpret_cast<const unsigned char*>(src) + gi);
+        }
+#pragma unroll
+        for (int cc = 0; cc < NC; ++cc) {
+            const int c = lane + cc * 32;
+            if (c >= COLS) break;
+            const int xx = x0 - Geo::R + c;
+            const uint32_t val = (CLAMP || (yin && xx >= 0 && xx < nx)) ? v[cc] : 0u;
+            const int e = dbase + c;
+            if (fmt == FMT_F32)
+                reinterpret_cast<uint32_t*>(raw)[e] = val;
+            else if (fmt == FMT_U16)
+                reinterpret_cast<uint16_t*>(raw)[e] = static_cast<uint16_t>(val);
+            else
+                raw[e] = static_cast<unsigned char>(val);
         }
     }
 }
@@ -185,10 +273,12 @@ struct ConvPlan {
     static constexpr int NG = (Geo::FH * Geo::FGROUPS + NT - 1) / NT;
     int off[NG][4];
 
-    __device__ __forceinline__ void init(int fmt, int nx, int ny, int x0, int y0, int tid)
+    // rows: the stage is filled by row copies (row pitch Geo::row_pitch), not by one TMA box
+    __device__ __forceinline__ void init(int fmt, int nx, int ny, int x0, int y0, int tid,
+                                         bool rows = false)
     {
         const int xa = fmt_xalign(fmt);
-        const int rw = Geo::raw_w(fmt);
+        const int rw = rows ? Geo::row_pitch(fmt) / fmt_bytes(fmt) : Geo::raw_w(fmt);
 #pragma unroll
         for (int n = 0; n < NG; ++n) {
             const int gi = tid + n * NT;
@@ -225,6 +315,36 @@ struct ConvPlan {
                 v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
             } else {
                 v = make_float4(raw[off[n][0]], raw[off[n][1]], raw[off[n][2]], raw[off[n][3]]);
+            }
+            reinterpret_cast<float4*>(F)[gi] = v;
+        }
+    }
+
+    // the same for a stage filled by issue_rows (clamped conversion only): each row's
+    // elements sit row_shift_elems() further in; zterm = clamp(z) * ny * nx (mod 2^32)
+    __device__ __forceinline__ void convert_rows(const unsigned char* raw, int fmt, float* F,
+                                                 int tid, int nx, int ny, int x0, int y0,
+                                                 uint32_t zterm) const
+    {
+        static_assert(CLAMP, "row-copied stages hold only rows inside the volume");
+        const int xa = fmt_xalign(fmt);
+#pragma unroll
+        for (int n = 0; n < NG; ++n) {
+            const int gi = tid + n * NT;
+            if (NG * NT > Geo::FH * Geo::FGROUPS && gi >= Geo::FH * Geo::FGROUPS) break;
+            const int row = gi / Geo::FGROUPS;
+            const int gy = clampi(y0 - Geo::R + row, 0, ny - 1);
+            const int m = static_cast<int>(row_shift_elems(zterm, gy, nx, x0, xa, fmt));
+            float4 v;
+            if (fmt == FMT_F32) {
+                const float* r = reinterpret_cast<const float*>(raw) + m;
+                v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
+            } else if (fmt == FMT_U16) {
+                const uint16_t* r = reinterpret_cast<const uint16_t*>(raw) + m;
+                v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
+            } else {
+                const unsigned char* r = raw + m;
+                v = make_float4(r[off[n][0]], r[off[n][1]], r[off[n][2]], r[off[n][3]]);
             }
             reinterpret_cast<float4*>(F)[gi] = v;
         }

@@ -74,21 +74,21 @@ __global__ void __launch_bounds__(sep::NT, 2)
     }
 }
 
-size_t batch_smem(int k, int sfmt, bool comp)
+size_t batch_smem(int k, int sfmt, bool comp, bool rows)
 {
     if (comp) {
         switch (k) {
-        case 1: return sep::smem_bytes_comp<1>(sfmt);
-        case 3: return sep::smem_bytes_comp<3>(sfmt);
-        case 5: return sep::smem_bytes_comp<5>(sfmt);
-        default: return sep::smem_bytes_comp<7>(sfmt);
+        case 1: return sep::smem_bytes_comp<1>(sfmt, rows);
+        case 3: return sep::smem_bytes_comp<3>(sfmt, rows);
+        case 5: return sep::smem_bytes_comp<5>(sfmt, rows);
+        default: return sep::smem_bytes_comp<7>(sfmt, rows);
         }
     }
     switch (k) {
-    case 1: return sep::smem_bytes<1>(sfmt);
-    case 3: return sep::smem_bytes<3>(sfmt);
-    case 5: return sep::smem_bytes<5>(sfmt);
-    default: return sep::smem_bytes<7>(sfmt);
+    case 1: return sep::smem_bytes<1>(sfmt, rows);
+    case 3: return sep::smem_bytes<3>(sfmt, rows);
+    case 5: return sep::smem_bytes<5>(sfmt, rows);
+    default: return sep::smem_bytes<7>(sfmt, rows);
     }
 }
 
@@ -218,7 +218,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
         // per row, when the volume starts on a 16-byte boundary
         J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
-        smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0));
+        smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
         order.push_back({-static_cast<long>(J.k) * (J.zchunk + J.k - 1), static_cast<int>(j)});
     }
     std::stable_sort(order.begin(), order.end());
@@ -228,7 +228,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         const sep::Job& J = P.jobs[o.second];
         std::vector<int4>& dstv = J.comp ? comp_items : items;
         (J.comp ? smem_comp : smem_fast) = std::max(J.comp ? smem_comp : smem_fast,
-                                                    batch_smem(J.k, J.sfmt, J.comp != 0));
+                                                    batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
         for (int bz = 0; bz < J.chunks; ++bz)
             for (int by = 0; by < J.tiles_y; ++by)
                 for (int bx = 0; bx < J.tiles_x; ++bx) dstv.push_back(make_int4(o.second, bx, by, bz));

@@ -69,10 +69,10 @@ struct DirectCfg {
 };
 
 template <int K>
-__host__ __device__ constexpr size_t direct_smem_bytes(int sfmt)
+__host__ __device__ constexpr size_t direct_smem_bytes(int sfmt, bool rows)
 {
     using Geo = typename DirectCfg<K>::Geo;
-    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
 }
 
@@ -97,8 +97,12 @@ __device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, in
     }
 }
 
-// SF/DF: source and destination formats fixed at compile time (-1: read from the arguments)
-template <int K, bool ADJ, int SF = -1, int DF = -1>
+// SF/DF: source and destination formats fixed at compile time (-1: read from the arguments);
+// LM: how stages are filled, fixed at compile time where known (the plane loop is unrolled,
+// so code for unused ways of loading costs instruction cache): 0 = from the arguments
+// (tensor map, row copies or plain loads), 1 = tensor map, 2 = row copies
+constexpr int LM_ANY = 0, LM_TMA = 1, LM_ROWS = 2;
+template <int K, bool ADJ, int SF = -1, int DF = -1, int LM = LM_ANY>
 __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
@@ -111,7 +115,9 @@ __global__ void __launch_bounds__(NT)
     const int sfmt = SF >= 0 ? SF : p.sfmt;
     const int dfmt = DF >= 0 ? DF : p.dfmt;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const int rawb = Geo::raw_bytes(sfmt);
+    const bool tma = LM == LM_TMA || (LM == LM_ANY && p.use_tma);
+    const bool rows = !ADJ && (LM == LM_ROWS || (LM == LM_ANY && p.rows));
+    const int rawb = Geo::stage_bytes(sfmt, rows);
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
@@ -129,13 +135,12 @@ __global__ void __launch_bounds__(NT)
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
-        if (p.use_tma) prefetch_tensor_map(&tmap);
+        if (LM != LM_ROWS && p.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
     int issued = 0;   // planes handed to the TMA unit so far (thread 0 only)
-    const bool rows = !ADJ && p.rows;
     const uint64_t vol_bytes = static_cast<uint64_t>(p.nx) * p.ny * p.nz * fmt_bytes(sfmt);
-    if (p.use_tma && tid == 0) {
+    if (tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             if (s == 0 && p.withhold_first) continue;
             mbar_arrive_expect_tx(&bars[s], txb);
@@ -181,7 +186,7 @@ __global__ void __launch_bounds__(NT)
         const unsigned char* rs = raw + s * rawb;
         float* Fb = F + (it & 1) * FH * FP;
         bool ok = true;
-        if (p.use_tma || rows) {
+        if (tma || rows) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, sfmt, p.nx,
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(NT)
             ++issued;
         }
         pend = -1;
-        if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
+        if (tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
                         ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1));
@@ -383,12 +388,20 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     // needs the zero extension a tensor map or the plain loads give)
     a.rows = (!ADJ && !a.use_tma && reinterpret_cast<uintptr_t>(job.src) % 16 == 0) ? 1 : 0;
 
-    const size_t smem = direct_smem_bytes<K>(job.sfmt);
+    const size_t smem = direct_smem_bytes<K>(job.sfmt, a.rows != 0);
     // the common float32 destinations get kernels with their formats compiled in
-    auto kern = k_direct<K, ADJ>;
+    // tensor-map jobs get kernels without the other ways of loading, and so do row-copy
+    // jobs of the compiled-in formats; plain-load jobs take the run-time variant
+    auto kern = a.use_tma ? k_direct<K, ADJ, -1, -1, LM_TMA> : k_direct<K, ADJ, -1, -1, LM_ANY>;
     if constexpr (!ADJ && K >= 3 && K <= 5) {
-        if (job.dfmt == FMT_F32 && job.sfmt == FMT_U8) kern = k_direct<K, ADJ, FMT_U8, FMT_F32>;
-        if (job.dfmt == FMT_F32 && job.sfmt == FMT_F32) kern = k_direct<K, ADJ, FMT_F32, FMT_F32>;
+        if (job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
+            if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA>;
+            else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS>;
+        }
+        if (job.dfmt == FMT_F32 && job.sfmt == FMT_F32) {
+            if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA>;
+            else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS>;
+        }
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));

@@ -23,6 +23,10 @@ constexpr int BX = 16, BY = 16;
 constexpr int RX = 4, RY = 2;
 constexpr int TX = BX * RX, TY = BY * RY;
 constexpr int STAGES = 4;
+// How a brick fills its stages, fixed at compile time where the caller knows it (the plane
+// loop is unrolled k times, so code for unused ways costs instruction cache):
+// LM_ANY reads the job's use_tma / rows flags (else plain loads), LM_TMA and LM_ROWS assume one.
+enum : int { LM_ANY = 0, LM_TMA = 1, LM_ROWS = 2 };
 // the y and z passes run as packed two-lane FMAs over output pairs (x, x+1) for k <= 5 (at
 // k >= 7, and in the run-time-format kernels at k = 5, the register pairs cost spills or
 // more than the halved FMA issue saves); SF: the compile-time source format or -1
@@ -53,10 +57,10 @@ struct W {
 };
 
 template <int K>
-__host__ __device__ constexpr size_t smem_bytes(int sfmt)
+__host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 {
     using Geo = Brick<K, TX, TY>;
-    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +      // float tile
            static_cast<size_t>(Geo::FH) * TX * sizeof(float);            // x-pass output
 }
@@ -73,7 +77,7 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // TMA so far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring and its
 // barrier phases carry on across bricks.  Returns false if a bounded wait timed out (after recording it and
 // draining the loads in flight).
-template <int K, class Wt, int SF = -1, int DF = -1>
+template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
@@ -87,7 +91,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const int sfmt = SF >= 0 ? SF : J.sfmt;
     const int dfmt = DF >= 0 ? DF : J.dfmt;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const int rawb = Geo::raw_bytes(sfmt);
+    const bool tma = LM == LM_TMA || (LM == LM_ANY && J.use_tma);
+    const bool rows = LM == LM_ROWS || (LM == LM_ANY && J.rows);
+    const int rawb = Geo::stage_bytes(sfmt, rows);
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
@@ -107,14 +113,14 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     int issued = 0;
     const uint64_t vol_bytes =
         static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(sfmt);
-    if (J.use_tma && tid == 0) {
+    if (tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
             mbar_arrive_expect_tx(&bars[q % STAGES], txb);
             tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
-    } else if (J.rows) {
+    } else if (rows) {
         for (int s = 0; s < STAGES && s < nplanes; ++s) {
             const uint32_t q = g0 + s;
             issue_rows<Geo, NT>(raw + (q % STAGES) * rawb, &bars[q % STAGES], J.src, vol_bytes,
@@ -126,7 +132,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     }
 
     ConvPlan<Geo, NT> plan;
-    plan.init(sfmt, J.nx, J.ny, x0, y0, tid, J.rows != 0);
+    plan.init(sfmt, J.nx, J.ny, x0, y0, tid, rows);
 
     // accumulators of the K output planes.  Packed kernels pair outputs (x, x+1) in one
     // float2, start at zero once, and afterwards give a slot's first tap in its z-march
@@ -157,7 +163,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
-        if (J.use_tma || J.rows) {
+        if (tma || rows) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, sfmt, J.nx, J.ny,
@@ -165,7 +171,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             __syncthreads();
         }
         if (ok) {
-            if (J.rows) {
+            if (rows) {
                 const uint32_t zterm = static_cast<uint32_t>(clampi(pfirst + it, 0, J.nz - 1)) *
                                        static_cast<uint32_t>(J.ny) * static_cast<uint32_t>(J.nx);
                 plan.convert_rows(rs, sfmt, F, tid, J.nx, J.ny, x0, y0, zterm);
@@ -177,12 +183,12 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             failed = true;
             return;
         }
-        if (J.use_tma && tid == 0 && it + STAGES < nplanes) {
+        if (tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
                         clampi(pfirst + it + STAGES, 0, J.nz - 1));
             ++issued;
-        } else if (J.rows && it + STAGES < nplanes) {
+        } else if (rows && it + STAGES < nplanes) {
             // all threads; the arrival follows the x-pass barrier below
             issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, sfmt, J.nx, J.ny,
                                 J.nz, x0, y0, pfirst + it + STAGES, tid);
@@ -209,7 +215,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         }
         __syncthreads();
         // the stage refilled by row copies above is complete in expectation: one arrival
-        if (J.rows && tid == 0 && it + STAGES < nplanes) {
+        if (rows && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive(&bars[s]);
             ++issued;
         }
@@ -309,7 +315,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         }
     }
     // only bricks loaded through the stage barriers move them through their phases
-    if (J.use_tma || J.rows) gplane = g0 + nplanes;
+    if (tma || rows) gplane = g0 + nplanes;
 
     if (failed) {
         if (tid == 0) {
@@ -378,15 +384,15 @@ __device__ __forceinline__ unsigned comp_code(float s, float c, float a0h, float
 }
 
 template <int K>
-__host__ __device__ constexpr size_t smem_bytes_comp(int sfmt)
+__host__ __device__ constexpr size_t smem_bytes_comp(int sfmt, bool rows = false)
 {
     using Geo = Brick<K, TX, CTY>;
-    return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(sfmt) +
+    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +
            static_cast<size_t>(Geo::FH) * TX * sizeof(float2);           // (hi, lo) x pass
 }
 
-template <int K, class Wt>
+template <int K, class Wt, int LM = LM_ANY>
 __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUtensorMap* tmap,
                                            int bx, int by, int bz, unsigned char* smem,
                                            uint32_t& gplane, unsigned* status)
@@ -397,7 +403,9 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
     constexpr int XITEMS = FH * XGROUPS;
 
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const int rawb = Geo::raw_bytes(J.sfmt);
+    const bool tma = LM == LM_TMA || (LM == LM_ANY && J.use_tma);
+    const bool rows = LM == LM_ROWS || (LM == LM_ANY && J.rows);
+    const int rawb = Geo::stage_bytes(J.sfmt, rows);
     const uint32_t txb = Geo::raw_tx(J.sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
@@ -417,14 +425,14 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
     int issued = 0;
     const uint64_t vol_bytes =
         static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(J.sfmt);
-    if (J.use_tma && tid == 0) {
+    if (tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
             mbar_arrive_expect_tx(&bars[q % STAGES], txb);
             tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
-    } else if (J.rows) {
+    } else if (rows) {
         for (int s = 0; s < STAGES && s < nplanes; ++s) {
             const uint32_t q = g0 + s;
             issue_rows<Geo, NT>(raw + (q % STAGES) * rawb, &bars[q % STAGES], J.src, vol_bytes,
@@ -435,7 +443,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % STAGES]);
     }
     ConvPlan<Geo, NT> plan;
-    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid, J.rows != 0);
+    plan.init(J.sfmt, J.nx, J.ny, x0, y0, tid, rows);
 
     float acc_s[K][RX], acc_c[K][RX];
 #pragma unroll
@@ -453,7 +461,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
-        if (J.use_tma || J.rows) {
+        if (tma || rows) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, J.sfmt, J.nx, J.ny,
@@ -461,7 +469,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             __syncthreads();
         }
         if (ok) {
-            if (J.rows) {
+            if (rows) {
                 const uint32_t zterm = static_cast<uint32_t>(clampi(pfirst + it, 0, J.nz - 1)) *
                                        static_cast<uint32_t>(J.ny) * static_cast<uint32_t>(J.nx);
                 plan.convert_rows(rs, J.sfmt, F, tid, J.nx, J.ny, x0, y0, zterm);
@@ -473,12 +481,12 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             failed = true;
             return;
         }
-        if (J.use_tma && tid == 0 && it + STAGES < nplanes) {
+        if (tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
                         clampi(pfirst + it + STAGES, 0, J.nz - 1));
             ++issued;
-        } else if (J.rows && it + STAGES < nplanes) {
+        } else if (rows && it + STAGES < nplanes) {
             // all threads; the arrival follows the x-pass barrier below
             issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, J.sfmt, J.nx, J.ny,
                                 J.nz, x0, y0, pfirst + it + STAGES, tid);
@@ -502,7 +510,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
         }
         __syncthreads();
         // the stage refilled by row copies above is complete in expectation: one arrival
-        if (J.rows && tid == 0 && it + STAGES < nplanes) {
+        if (rows && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive(&bars[s]);
             ++issued;
         }
@@ -553,7 +561,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             plane(it, u);
         }
     }
-    if (J.use_tma || J.rows) gplane = g0 + nplanes;
+    if (tma || rows) gplane = g0 + nplanes;
     if (failed) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);

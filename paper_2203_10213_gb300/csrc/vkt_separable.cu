@@ -15,8 +15,9 @@ namespace {
 template <int K, int SF>
 constexpr int sep_min_blocks() { return (K <= 3 || (K <= 5 && SF < 0)) ? 3 : 2; }
 
-// SF/DF: source and destination formats fixed at compile time (-1: read from the job)
-template <int K, int SF = -1, int DF = -1>
+// SF/DF: source and destination formats fixed at compile time (-1: read from the job);
+// LM: the way stages are filled (sep::LM_*), fixed at compile time where known
+template <int K, int SF = -1, int DF = -1, int LM = sep::LM_ANY>
 __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     k_separable(const __grid_constant__ CUtensorMap tmap, const sep::Job J, const sep::W<K> G,
                 unsigned* status)
@@ -24,15 +25,15 @@ __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     extern __shared__ __align__(128) unsigned char smem[];
     if (threadIdx.x == 0) {
         sep::init_barriers(smem);
-        if (J.use_tma) prefetch_tensor_map(&tmap);
+        if (LM != sep::LM_ROWS && J.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick<K, sep::W<K>, SF, DF>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
-                                     gplane, status);
+    sep::brick<K, sep::W<K>, SF, DF, LM>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
+                                         gplane, status);
 }
 
-template <int K>
+template <int K, int LM = sep::LM_ANY>
 __global__ void __launch_bounds__(sep::NT)
     k_separable_comp(const __grid_constant__ CUtensorMap tmap, const sep::Job J,
                      const sep::W<K> G, unsigned* status)
@@ -40,11 +41,27 @@ __global__ void __launch_bounds__(sep::NT)
     extern __shared__ __align__(128) unsigned char smem[];
     if (threadIdx.x == 0) {
         sep::init_barriers(smem);
-        if (J.use_tma) prefetch_tensor_map(&tmap);
+        if (LM != sep::LM_ROWS && J.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick_comp<K>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem, gplane, status);
+    sep::brick_comp<K, sep::W<K>, LM>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
+                                      gplane, status);
+}
+
+// the kernel for a job: tensor-map jobs and (for the compiled-in formats) row-copy jobs get
+// kernels without the other ways of loading; plain-load jobs take the run-time variant
+template <int K, int SF, int DF>
+auto pick_fast(const sep::Job& J)
+{
+    if constexpr (SF >= 0) {
+        if (J.use_tma) return k_separable<K, SF, DF, sep::LM_TMA>;
+        if (J.rows) return k_separable<K, SF, DF, sep::LM_ROWS>;
+        return k_separable<K, -1, -1, sep::LM_ANY>;
+    } else {
+        if (J.use_tma) return k_separable<K, -1, -1, sep::LM_TMA>;
+        return k_separable<K, -1, -1, sep::LM_ANY>;
+    }
 }
 
 template <int K>
@@ -95,15 +112,16 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     // per row, when the volume starts on a 16-byte boundary
     J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
     if (!J.use_tma) memset(&map, 0, sizeof(map));
-    const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt) : sep::smem_bytes<K>(job.sfmt);
+    const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt, J.rows != 0)
+                               : sep::smem_bytes<K>(job.sfmt, J.rows != 0);
     // the common float32 destinations get kernels with their formats compiled in
-    auto fast = k_separable<K>;
+    auto fast = pick_fast<K, -1, -1>(J);
     if constexpr (K >= 3 && K <= 7) {
-        if (!J.comp && J.dfmt == FMT_F32 && (J.sfmt == FMT_U8 || J.sfmt == FMT_F32)) {
-            fast = J.sfmt == FMT_U8 ? k_separable<K, FMT_U8, FMT_F32> : k_separable<K, FMT_F32, FMT_F32>;
-        }
+        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_U8) fast = pick_fast<K, FMT_U8, FMT_F32>(J);
+        if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_F32) fast = pick_fast<K, FMT_F32, FMT_F32>(J);
     }
-    cudaError_t e = J.comp ? cudaFuncSetAttribute(k_separable_comp<K>,
+    auto comp = J.use_tma ? k_separable_comp<K, sep::LM_TMA> : k_separable_comp<K, sep::LM_ANY>;
+    cudaError_t e = J.comp ? cudaFuncSetAttribute(comp,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem))
                            : cudaFuncSetAttribute(fast,
@@ -116,7 +134,7 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                 J.use_tma, J.rows);
     const dim3 grid(J.tiles_x, J.tiles_y, J.chunks);
     if (J.comp)
-        k_separable_comp<K><<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
+        comp<<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
     else
         fast<<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
     count_launches(1);

@@ -140,8 +140,14 @@ struct Brick {
     // row pitch (bytes) of a stage filled by row copies: a raw row plus up to 15 bytes of
     // 16-byte misalignment in front of it
     __host__ __device__ static constexpr int row_pitch(int fmt) { return raw_w(fmt) * fmt_bytes(fmt) + 16; }
-    // the (128-byte padded) size of one raw stage, enough for either way of filling it
-    __host__ __device__ static constexpr int raw_bytes(int fmt) { return (FH * row_pitch(fmt) + 127) & ~127; }
+    // the (128-byte padded) size of one raw stage filled by a TMA box or plain loads, and of
+    // one filled by row copies
+    __host__ __device__ static constexpr int raw_bytes(int fmt) { return (raw_tx(fmt) + 127) & ~127; }
+    __host__ __device__ static constexpr int rows_bytes(int fmt) { return (FH * row_pitch(fmt) + 127) & ~127; }
+    __host__ __device__ static constexpr int stage_bytes(int fmt, bool rows)
+    {
+        return rows ? rows_bytes(fmt) : raw_bytes(fmt);
+    }
 };
 
 // Row-copy loading, for volumes whose rows are not a multiple of 16 bytes long (no tensor

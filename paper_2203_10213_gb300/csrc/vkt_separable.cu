@@ -10,10 +10,10 @@
 namespace vkt {
 namespace {
 
-// CTAs per SM the register allocation must allow: three where that costs no spills (k = 3,
-// and the run-time-format kernels up to k = 5), else two
+// CTAs per SM the register allocation must allow: three up to k = 5 (the tensor-map kernels
+// fit in 80 registers without spills there), else two
 template <int K, int SF>
-constexpr int sep_min_blocks() { return (K <= 3 || (K <= 5 && SF < 0)) ? 3 : 2; }
+constexpr int sep_min_blocks() { return K <= 5 ? 3 : 2; }
 
 // SF/DF: source and destination formats fixed at compile time (-1: read from the job);
 // LM: the way stages are filled (sep::LM_*), fixed at compile time where known

@@ -222,6 +222,22 @@ VKT_API vktError vktFilterDestroy(vktFilter filter);
 VKT_API vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter);
 
 /*
+ * Range version of ApplyFilter (Sec. 3.2: range algorithms operate on a region of interest
+ * given as an axis-aligned box in cell coordinates; the name appends "Range").  Only the
+ * dst voxels in [firstX, lastX) x [firstY, lastY) x [firstZ, lastZ) are written, with the
+ * values vktApplyFilterSV would give them: the taps read the real neighbours of the region,
+ * clamped at the volume's faces, not at the region's.  All other dst voxels keep their
+ * contents.  The box must satisfy 0 <= first <= last <= dims on every axis (else
+ * INVALID_VALUE); an empty box writes nothing.  The other rules are those of
+ * vktApplyFilterSV; the tensor-core path filters whole volumes only (UNSUPPORTED when the
+ * policy forces it here; VKT_PATH_AUTO uses the direct or separable path).
+ */
+VKT_API vktError vktApplyFilterRangeSV(vktStructuredVolume dst, vktStructuredVolume src,
+                                       vktFilter filter, int32_t firstX, int32_t firstY,
+                                       int32_t firstZ, int32_t lastX, int32_t lastY,
+                                       int32_t lastZ);
+
+/*
  * Batched ApplyFilter over n independent (dst[i], src[i], filters[i]) triples, with
  * the rules of vktApplyFilterSV for each triple, in one persistent launch over a
  * work list of bricks.  The launch is captured in a CUDA graph that is reused while

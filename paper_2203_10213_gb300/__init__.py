@@ -309,11 +309,18 @@ class Filter:
 # ------------------------------------------------------------------ ApplyFilter
 
 def apply_filter(dst: StructuredVolume, src: StructuredVolume, filt: Filter, path=None,
-                 stream=None) -> None:
+                 stream=None, roi=None) -> None:
     """Enqueues dst = filter(src) on `stream` (default: torch's current stream); path None
-    keeps the thread policy's path."""
+    keeps the thread policy's path.  roi ((x0, y0, z0), (x1, y1, z1)): only the voxels of
+    that half-open box are written (vktApplyFilterRangeSV)."""
     with policy(stream=stream, path=path):
-        check(_lib.vktApplyFilterSV(dst.handle, src.handle, filt.handle), "vktApplyFilterSV")
+        if roi is None:
+            check(_lib.vktApplyFilterSV(dst.handle, src.handle, filt.handle), "vktApplyFilterSV")
+        else:
+            (x0, y0, z0), (x1, y1, z1) = roi
+            check(_lib.vktApplyFilterRangeSV(dst.handle, src.handle, filt.handle, int(x0), int(y0),
+                                             int(z0), int(x1), int(y1), int(z1)),
+                  "vktApplyFilterRangeSV")
 
 
 def apply_filter_batch(dsts, srcs, filters, stream=None) -> None:
@@ -339,14 +346,15 @@ def apply_filter_backward(grad_src, grad_weights, grad_dst: StructuredVolume,
 
 
 def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
-                  dst_range=(0.0, 1.0), path=None, out=None):
-    """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor."""
+                  dst_range=(0.0, 1.0), path=None, out=None, roi=None):
+    """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor (roi:
+    see apply_filter; voxels outside it keep the contents of `out`)."""
     torch = _torch()
     if out is None:
         out = torch.empty(src_t.shape, dtype=dst_dtype or torch.float32, device=src_t.device)
     src = StructuredVolume.from_tensor(src_t, *src_range)
     dst = StructuredVolume.from_tensor(out, *dst_range)
-    apply_filter(dst, src, filt, path=path)
+    apply_filter(dst, src, filt, path=path, roi=roi)
     return out
 
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "vktFilterGetSeparableWeights": [p, pf, pf, pf],
     "vktFilterDestroy": [p],
     "vktApplyFilterSV": [p, p, p],
+    "vktApplyFilterRangeSV": [p, p, p, i32, i32, i32, i32, i32, i32],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],

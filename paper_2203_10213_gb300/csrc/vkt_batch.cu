@@ -201,6 +201,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         J.nx = s->dims[0];
         J.ny = s->dims[1];
         J.nz = s->dims[2];
+        sep::set_whole_volume(J);
         J.sfmt = s->format;
         J.dfmt = dst[i]->format;
         J.k = filters[i]->k;
@@ -311,7 +312,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     for (size_t q = 0; q < dense_idx.size() && err == VKT_NO_ERROR; ++q) {
         const int i = dense_idx[q];
         const vktFilter_impl* f = filters[i];
-        Job job;
+        Job job{};
         job.src = src[i]->data;
         job.dst = dst[i]->data;
         job.nx = src[i]->dims[0];

@@ -47,6 +47,7 @@ struct DirectArgs {
     int nx, ny, nz;
     int ox0, oy0, oz0;     // origin of the output domain (0, or the padded domain's corner)
     int ex, ey, ez;        // extent of the output domain
+    int sx0, sx1, sy1;     // forward: voxels with x in [sx0, sx1) and y < sy1 are stored
     int sfmt, dfmt;
     int zchunk;
     int use_tma;
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(NT)
     };
 
     const int ox = x0 + tx * RX;
-    const int nvalid = p.nx - ox;
+    const int nvalid = p.sx1 - ox;
+    const int first = p.sx0 > ox ? p.sx0 - ox : 0;   // leading columns outside the region
     bool failed = false;
 
     // One input plane: fetch, convert, multiply into the K output planes, retire one.
@@ -277,9 +279,9 @@ __global__ void __launch_bounds__(NT)
                 if (ADJ) {
                     store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
                                           ox, row);
-                } else if (oy < p.ny && nvalid > 0) {
+                } else if (oy < p.sy1 && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
-                    store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax);
+                    store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
                 }
             }
         }
@@ -351,11 +353,23 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         a.ex = job.nx + R - a.ox0;
         a.ey = job.ny + 2 * R;
         a.ez = job.nz + 2 * R;
+        a.sx0 = 0;
+        a.sx1 = job.nx;
+        a.sy1 = job.ny;
     } else {
-        a.ox0 = a.oy0 = a.oz0 = 0;
-        a.ex = job.nx;
-        a.ey = job.ny;
-        a.ez = job.nz;
+        // output region; the tiles start on a 16-byte boundary left of it (tensor-map boxes
+        // start there) and store only inside it
+        int rx0, ry0, rz0, rx1, ry1, rz1;
+        job_region(job, rx0, ry0, rz0, rx1, ry1, rz1);
+        a.ox0 = rx0 - rx0 % fmt_xalign(job.sfmt);
+        a.oy0 = ry0;
+        a.oz0 = rz0;
+        a.ex = rx1 - a.ox0;
+        a.ey = ry1 - ry0;
+        a.ez = rz1 - rz0;
+        a.sx0 = rx0;
+        a.sx1 = rx1;
+        a.sy1 = ry1;
     }
     DenseW<K> W;
     const int kk = K * K * K;

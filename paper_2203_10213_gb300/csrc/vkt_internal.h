@@ -31,19 +31,37 @@ namespace vkt {
 
 // One filter application as the kernels see it.
 struct Job {
-    const void* src;
-    void* dst;
-    int nx, ny, nz;
-    int sfmt, dfmt;     // vktDataFormat values
+    // every member starts at zero, so a job left partly unset filters the whole volume
+    const void* src = nullptr;
+    void* dst = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    int sfmt = 0, dfmt = 0;     // vktDataFormat values
     // Epilogue: the kernels accumulate acc = sum w * q over stored source values q and
     // write a0 + a1*acc (float dst), or clamp(rint(a0 + a1*acc), 0, qmax) (integer dst).
-    float a0, a1, qmax;
+    float a0 = 0.f, a1 = 0.f, qmax = 0.f;
     // Compensated accumulation (separable path, integer destinations): set when an FP32
     // error bound does not keep the code within 1e-3 LSB of exact; a0lo/a1lo carry the
     // low halves of a0/a1 as double-float pairs.
-    int comp;
-    float a0lo, a1lo;
+    int comp = 0;
+    float a0lo = 0.f, a1lo = 0.f;
+    // Output region of interest (Sec. 3.2, "range" algorithms): when roi is set, only voxels
+    // in [rx0, rx1) x [ry0, ry1) x [rz0, rz1) (cell coordinates) are written; the taps still
+    // read the real neighbours, clamped at the volume's faces.  Otherwise the whole volume.
+    int roi = 0;
+    int rx0 = 0, ry0 = 0, rz0 = 0, rx1 = 0, ry1 = 0, rz1 = 0;
 };
+
+// the output region of a job as [x0, x1) x [y0, y1) x [z0, z1)
+inline void job_region(const Job& j, int& x0, int& y0, int& z0, int& x1, int& y1, int& z1)
+{
+    if (j.roi) {
+        x0 = j.rx0; y0 = j.ry0; z0 = j.rz0;
+        x1 = j.rx1; y1 = j.ry1; z1 = j.rz1;
+    } else {
+        x0 = y0 = z0 = 0;
+        x1 = j.nx; y1 = j.ny; z1 = j.nz;
+    }
+}
 
 struct Ctx {
     cudaStream_t stream;

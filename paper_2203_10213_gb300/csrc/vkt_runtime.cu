@@ -578,13 +578,11 @@ vktError vktFilterDestroy(vktFilter f)
 
 // ------------------------------------------------------------------ ApplyFilter
 
-vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter)
+// ApplyFilter on the whole volume (box == nullptr) or on the region
+// [box[0], box[3]) x [box[1], box[4]) x [box[2], box[5]) (validated by the caller)
+static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter,
+                             const int32_t* box)
 {
-    if (!valid(dst) || !valid(src) || !valid(filter)) return VKT_ERROR_INVALID_HANDLE;
-    if (dst->dims[0] != src->dims[0] || dst->dims[1] != src->dims[1] ||
-        dst->dims[2] != src->dims[2])
-        return VKT_ERROR_DIMS_MISMATCH;
-    if (overlaps(dst, src)) return VKT_ERROR_INVALID_VALUE;
     Ctx ctx;
     vktError err = get_context(&ctx);
     if (err != VKT_NO_ERROR) return err;
@@ -594,18 +592,28 @@ vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktF
     if (path == VKT_PATH_AUTO) {
         if (filter->separable)
             path = VKT_PATH_SEPARABLE;
-        else if (k >= 5 && tensor_available(dst, src, filter) == VKT_NO_ERROR)
+        else if (!box && k >= 5 && tensor_available(dst, src, filter) == VKT_NO_ERROR)
             path = VKT_PATH_TENSOR;
         else
             path = VKT_PATH_DIRECT;
     }
     if (path == VKT_PATH_SEPARABLE && !filter->separable) return VKT_ERROR_UNSUPPORTED;
     if (path == VKT_PATH_TENSOR) {
+        if (box) return VKT_ERROR_UNSUPPORTED;   // the tensor-core path filters whole volumes
         err = tensor_available(dst, src, filter);
         if (err != VKT_NO_ERROR) return err;
     }
 
-    Job job;
+    Job job{};
+    if (box) {
+        job.roi = 1;
+        job.rx0 = box[0];
+        job.ry0 = box[1];
+        job.rz0 = box[2];
+        job.rx1 = box[3];
+        job.ry1 = box[4];
+        job.rz1 = box[5];
+    }
     job.src = src->data;
     job.dst = dst->data;
     job.nx = src->dims[0];
@@ -642,12 +650,48 @@ vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktF
         cudaEventSynchronize(ev[1]);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        fprintf(stderr, "[vkt] ApplyFilter %dx%dx%d k=%d path=%d: %.3f ms\n", job.nx, job.ny,
-                job.nz, k, path, ms);
+        fprintf(stderr, "[vkt] ApplyFilter%s %dx%dx%d k=%d path=%d: %.3f ms\n",
+                box ? "Range" : "", job.nx, job.ny, job.nz, k, path, ms);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
     }
     return err;
+}
+
+static vktError check_filter_args(vktStructuredVolume dst, vktStructuredVolume src,
+                                  vktFilter filter)
+{
+    if (!valid(dst) || !valid(src) || !valid(filter)) return VKT_ERROR_INVALID_HANDLE;
+    if (dst->dims[0] != src->dims[0] || dst->dims[1] != src->dims[1] ||
+        dst->dims[2] != src->dims[2])
+        return VKT_ERROR_DIMS_MISMATCH;
+    if (overlaps(dst, src)) return VKT_ERROR_INVALID_VALUE;
+    return VKT_NO_ERROR;
+}
+
+vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter)
+{
+    const vktError err = check_filter_args(dst, src, filter);
+    if (err != VKT_NO_ERROR) return err;
+    return apply_filter(dst, src, filter, nullptr);
+}
+
+vktError vktApplyFilterRangeSV(vktStructuredVolume dst, vktStructuredVolume src,
+                               vktFilter filter, int32_t firstX, int32_t firstY, int32_t firstZ,
+                               int32_t lastX, int32_t lastY, int32_t lastZ)
+{
+    const vktError err = check_filter_args(dst, src, filter);
+    if (err != VKT_NO_ERROR) return err;
+    const int32_t box[6] = {firstX, firstY, firstZ, lastX, lastY, lastZ};
+    for (int a = 0; a < 3; ++a)
+        if (box[a] < 0 || box[a] > box[a + 3] || box[a + 3] > src->dims[a])
+            return VKT_ERROR_INVALID_VALUE;
+    if (box[0] == box[3] || box[1] == box[4] || box[2] == box[5]) {
+        // an empty region writes nothing; the device is still required, as for any call
+        Ctx ctx;
+        return get_context(&ctx);
+    }
+    return apply_filter(dst, src, filter, box);
 }
 
 vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeights,
@@ -675,7 +719,7 @@ vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeight
         // face voxels of dL/dsrc are accumulated atomically: start from zero
         cudaError_t e = cudaMemsetAsync(gradSrc->data, 0, volume_bytes(gradSrc), ctx.stream);
         if (e != cudaSuccess) return from_cuda(e);
-        Job job;
+        Job job{};
         job.src = gradDst->data;
         job.dst = gradSrc->data;
         job.nx = nx;

@@ -42,6 +42,10 @@ struct Job {
     int zchunk;
     int use_tma;
     int rows;          // no tensor map: stages filled by per-row bulk copies (issue_rows)
+    // output region: bricks start at (ox0, oy0, oz0) and store the voxels with x in
+    // [sx0, sx1), y < sy1, z < sz1 (the whole volume: set_whole_volume)
+    int ox0, oy0, oz0;
+    int sx0, sx1, sy1, sz1;
     int k;
     int tiles_x, tiles_y, chunks;
     float a0, a1, qmax;
@@ -50,6 +54,15 @@ struct Job {
     int comp;
     float a0lo, a1lo;
 };
+
+inline void set_whole_volume(Job& J)
+{
+    J.ox0 = J.oy0 = J.oz0 = 0;
+    J.sx0 = 0;
+    J.sx1 = J.nx;
+    J.sy1 = J.ny;
+    J.sz1 = J.nz;
+}
 
 template <int K>
 struct W {
@@ -101,9 +114,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int x0 = bx * TX, y0 = by * TY;
-    const int zc0 = bz * J.zchunk;
-    const int zc1 = min(zc0 + J.zchunk, J.nz);
+    const int x0 = J.ox0 + bx * TX, y0 = J.oy0 + by * TY;
+    const int zc0 = J.oz0 + bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, J.sz1);
     if (zc0 >= zc1) return true;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
@@ -155,7 +168,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             }
 
     const int ox = x0 + tx * RX;
-    const int nvalid = J.nx - ox;
+    const int nvalid = J.sx1 - ox;
+    const int first = J.sx0 > ox ? J.sx0 - ox : 0;   // leading columns outside the region
     bool failed = false;
 
     auto plane = [&](const int it, const int u) {
@@ -224,9 +238,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         // stores the completed output plane it - R (once it >= 2R)
         auto store_plane = [&](const float (&rowv)[RX], int i) {
             const int oy = y0 + ty * RY + i;
-            if (it >= 2 * R && oy < J.ny && nvalid > 0) {
+            if (it >= 2 * R && oy < J.sy1 && nvalid > 0) {
                 const int64_t idx = (static_cast<int64_t>(pfirst + it - R) * J.ny + oy) * J.nx + ox;
-                store_row<RX>(J.dst, dfmt, idx, nvalid, rowv, J.a0, J.a1, J.qmax);
+                store_row<RX>(J.dst, dfmt, idx, nvalid, rowv, J.a0, J.a1, J.qmax, first);
             }
         };
         if constexpr (PAIR) {
@@ -413,9 +427,9 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int x0 = bx * TX, y0 = by * CTY;
-    const int zc0 = bz * J.zchunk;
-    const int zc1 = min(zc0 + J.zchunk, J.nz);
+    const int x0 = J.ox0 + bx * TX, y0 = J.oy0 + by * CTY;
+    const int zc0 = J.oz0 + bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, J.sz1);
     if (zc0 >= zc1) return true;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
@@ -453,7 +467,8 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
 
     const int ox = x0 + tx * RX;
     const int oy = y0 + ty;
-    const int nvalid = J.nx - ox;
+    const int nvalid = J.sx1 - ox;
+    const int first = J.sx0 > ox ? J.sx0 - ox : 0;   // leading columns outside the region
     bool failed = false;
 
     auto plane = [&](const int it, const int u) {
@@ -534,12 +549,12 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             for (int x = 0; x < RX; ++x) dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
         }
         const int sl0 = ((u - R) % K + K) % K;
-        if (it >= 2 * R && oy < J.ny && nvalid > 0) {
+        if (it >= 2 * R && oy < J.sy1 && nvalid > 0) {
             const int oz = pfirst + it - R;
             const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
 #pragma unroll
             for (int x = 0; x < RX; ++x) {
-                if (x < nvalid) {
+                if (x >= first && x < nvalid) {
                     const unsigned code = comp_code(acc_s[sl0][x], acc_c[sl0][x], J.a0, J.a0lo,
                                                     J.a1, J.a1lo, J.qmax);
                     if (J.dfmt == FMT_U16)

@@ -85,6 +85,18 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     J.comp = job.comp;
     J.a0lo = job.a0lo;
     J.a1lo = job.a1lo;
+    // output region; the brick grid starts at a 16-byte boundary left of it (tensor-map
+    // boxes start there) and stores only inside it
+    int rx0, ry0, rz0, rx1, ry1, rz1;
+    job_region(job, rx0, ry0, rz0, rx1, ry1, rz1);
+    J.ox0 = rx0 - rx0 % fmt_xalign(job.sfmt);
+    J.oy0 = ry0;
+    J.oz0 = rz0;
+    J.sx0 = rx0;
+    J.sx1 = rx1;
+    J.sy1 = ry1;
+    J.sz1 = rz1;
+    const int ex = rx1 - J.ox0, ey = ry1 - ry0, ez = rz1 - rz0;
     const int ty = J.comp ? sep::CTY : sep::TY;
     sep::W<K> G;
     for (int i = 0; i < K; ++i) {
@@ -98,10 +110,10 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    J.zchunk = sep::choose_zchunk(job.nx, job.ny, job.nz, sms);
-    J.tiles_x = (job.nx + sep::TX - 1) / sep::TX;
-    J.tiles_y = (job.ny + ty - 1) / ty;
-    J.chunks = (job.nz + J.zchunk - 1) / J.zchunk;
+    J.zchunk = sep::choose_zchunk(ex, ey, ez, sms);
+    J.tiles_x = (ex + sep::TX - 1) / sep::TX;
+    J.tiles_y = (ey + ty - 1) / ty;
+    J.chunks = (ez + J.zchunk - 1) / J.zchunk;
 
     alignas(64) CUtensorMap map;
     J.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz,

@@ -377,24 +377,26 @@ __device__ __forceinline__ void load_row(const float* p, float (&v)[N])
     for (int i = N2; i < N; ++i) v[i] = p[i];
 }
 
-// Writes RX consecutive results of one row, mapped to the destination format.
+// Writes results first .. nvalid-1 of RX consecutive results of one row (from idx), mapped
+// to the destination format.
 template <int RX>
 __device__ __forceinline__ void store_row(void* dst, int dfmt, int64_t idx, int nvalid,
-                                          const float (&acc)[RX], float a0, float a1, float qmax)
+                                          const float (&acc)[RX], float a0, float a1, float qmax,
+                                          int first = 0)
 {
     float v[RX];
 #pragma unroll
     for (int x = 0; x < RX; ++x) v[x] = fmaf(a1, acc[x], a0);
     if (dfmt == FMT_F32) {
         float* d = reinterpret_cast<float*>(dst) + idx;
-        if (RX == 4 && nvalid >= 4 && (idx & 3) == 0) {
+        if (RX == 4 && first == 0 && nvalid >= 4 && (idx & 3) == 0) {
             *reinterpret_cast<float4*>(d) = make_float4(v[0], v[1], v[2], v[3]);
-        } else if (RX == 2 && nvalid >= 2 && (idx & 1) == 0) {
+        } else if (RX == 2 && first == 0 && nvalid >= 2 && (idx & 1) == 0) {
             *reinterpret_cast<float2*>(d) = make_float2(v[0], v[1]);
         } else {
 #pragma unroll
             for (int x = 0; x < RX; ++x)
-                if (x < nvalid) d[x] = v[x];
+                if (x >= first && x < nvalid) d[x] = v[x];
         }
         return;
     }
@@ -405,12 +407,12 @@ __device__ __forceinline__ void store_row(void* dst, int dfmt, int64_t idx, int 
         uint16_t* d = reinterpret_cast<uint16_t*>(dst) + idx;
 #pragma unroll
         for (int x = 0; x < RX; ++x)
-            if (x < nvalid) d[x] = static_cast<uint16_t>(q[x]);
+            if (x >= first && x < nvalid) d[x] = static_cast<uint16_t>(q[x]);
     } else {
         unsigned char* d = reinterpret_cast<unsigned char*>(dst) + idx;
 #pragma unroll
         for (int x = 0; x < RX; ++x)
-            if (x < nvalid) d[x] = static_cast<unsigned char>(q[x]);
+            if (x >= first && x < nvalid) d[x] = static_cast<unsigned char>(q[x]);
     }
 }
 

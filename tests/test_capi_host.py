@@ -105,6 +105,24 @@ def test_apply_filter_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+def test_apply_filter_range_validation_without_device(vkt, lib):
+    fake1, fake2 = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(a), fake1, 8, 6, 4, vkt.F32, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(b), fake2, 8, 6, 4, vkt.F32, 1, 1, 1, 0, 1) == 0
+    f = vkt.Filter.gaussian(3, 1.0)
+    R = lib.vktApplyFilterRangeSV
+    assert R(None, a, f.handle, 0, 0, 0, 1, 1, 1) == 2
+    for box in ((-1, 0, 0, 8, 6, 4), (0, 0, 0, 9, 6, 4), (0, 0, 0, 8, 7, 4), (0, 0, 0, 8, 6, 5),
+                (3, 0, 0, 2, 6, 4), (0, 5, 0, 8, 4, 4), (0, 0, 3, 8, 6, 2)):
+        assert R(a, b, f.handle, *box) == 1, box      # box outside the volume or reversed
+    # a valid box reaches the device check (no GPU here)
+    assert R(a, b, f.handle, 1, 1, 1, 7, 5, 3) == 6
+    assert R(a, b, f.handle, 2, 0, 0, 2, 6, 4) == 6     # empty box: still needs a device
+    for h in (a, b):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
 def test_owning_create_reports_missing_device(vkt, lib):
     import torch
     if torch.cuda.is_available():

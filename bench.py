@@ -368,6 +368,44 @@ def range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g, lap):
             **out}
 
 
+# ------------------------------------------------------------------ brick form
+
+def brick_form(vkt, torch, stream, src):
+    """BrickDecompose of the step's 512^3 uint8 volume into 64^3 bricks, without ghost cells
+    and with the 2 ghost cells a 5^3 filter needs: ms per call (device time of the call,
+    including its small brick-table upload) and GB/s on the algorithmic bytes (the source
+    read once, every brick voxel written once)."""
+    import ctypes
+    out = {}
+    for g in (0, 2):
+        bricks = vkt.brick_decompose(src, (64, 64, 64), g, stream=stream)
+        views = [vkt.StructuredVolume.from_tensor(t) for t in bricks]
+        arr = (ctypes.c_void_p * len(views))(*(v.handle.value for v in views))
+        sv = vkt.StructuredVolume.from_tensor(src)
+        reps = 10
+        with vkt.policy(stream=stream):
+            def call():
+                vkt.check(vkt._lib.vktBrickDecomposeSV(arr, len(views), sv.handle, 64, 64, 64, g))
+            for _ in range(3):
+                call()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                call()
+            b.record(stream)
+            torch.cuda.synchronize()
+            vkt.synchronize()
+        ms = a.elapsed_time(b) / reps
+        nbytes = src.numel() * src.element_size() + sum(t.numel() * t.element_size() for t in bricks)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[f"ghost{g}"] = {"bricks": len(bricks), "ms": round(ms, 4), "algorithmic_bytes": int(nbytes),
+                            "achieved_gbs": round(gbs, 1),
+                            "frac_hbm": round(gbs / measured_peaks()[0]["hbm_gbs"], 4)}
+        del views, bricks
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -520,6 +558,7 @@ def run_ours(args):
     bform = None
     if not args.no_batching_form:
         bform = batching_form(args, vkt, torch, dev, stream)
+    kform = brick_form(vkt, torch, stream, src)
     g_roi = vkt.Filter.gaussian(5, 1.5)
     rform = range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g_roi, lap)
     g_roi.destroy()
@@ -535,7 +574,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "precision_form": pform, "batching_form": bform,
-            "range_form": rform,
+            "range_form": rform, "brick_form": kform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

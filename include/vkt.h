@@ -293,6 +293,35 @@ VKT_API vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gr
 VKT_API vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStructuredVolume gradDst,
                                                    vktStructuredVolume src, vktFilter filter);
 
+/* ------------------------------------------------------------------ BrickDecompose */
+
+/*
+ * Number of bricks along each axis when `volume` is split into bricks of
+ * brickX x brickY x brickZ voxels: ceil(dims / brick).  INVALID_HANDLE for a bad volume,
+ * INVALID_VALUE for NULL outputs or a brick size < 1.  Needs no device.
+ */
+VKT_API vktError vktBrickDecomposeCountSV(int32_t* countX, int32_t* countY, int32_t* countZ,
+                                          vktStructuredVolume volume, int32_t brickX,
+                                          int32_t brickY, int32_t brickZ);
+
+/*
+ * BrickDecompose (Sec. 3.2, "domain decomposition algorithms": a volume split into subgrids,
+ * optionally with ghost cells for interpolation).  Brick (kx, ky, kz) covers the source
+ * voxels [o, o + s) with o = (kx*brickX, ky*brickY, kz*brickZ) and s = min(brick, dims - o)
+ * per axis; it is written to bricks[(kz*countY + ky)*countX + kx], a volume the caller
+ * created with dims s + 2*ghost and the source's format, whose voxel (i, j, k) becomes the
+ * source voxel clamp(o - ghost + (i, j, k)) (stored codes copied bit for bit): ghost cells
+ * inside the volume hold the neighbouring bricks' voxels, ghost cells beyond a face repeat
+ * the face voxel (clamp-to-edge, the boundary rule of ApplyFilter).  numBricks must equal
+ * countX*countY*countZ and ghost >= 0 (else INVALID_VALUE); a brick with the wrong dims gives
+ * DIMS_MISMATCH, one with another format, or overlapping the source, INVALID_VALUE.  The
+ * bricks must not overlap one another (not checked).  Asynchronous on the policy stream;
+ * the brick table is copied into stream-ordered device scratch for the call.
+ */
+VKT_API vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
+                                     vktStructuredVolume volume, int32_t brickX, int32_t brickY,
+                                     int32_t brickZ, int32_t ghost);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,7 +11,8 @@ Pins (tests/test_oracle.py): identity kernel, constant volume, linearity in inpu
 kernel, separable kernel = three 1-D clamped passes, hand-derived closed forms on small
 volumes (tests/golden), scipy.ndimage.correlate(mode="nearest") and torch float64
 replicate-padded conv3d, the adjoint dot-product identity, and central finite
-differences of a quadratic loss.
+differences of a quadratic loss.  ``brick_decompose`` (index arithmetic only, in numpy) is
+pinned by exact reassembly, neighbour agreement and face replication.
 """
 from __future__ import annotations
 
@@ -211,3 +212,22 @@ def backward_input_points(gy: np.ndarray, w, idx) -> np.ndarray:
 def error_scale(w, vmax_abs: float) -> float:
     """Normaliser of float errors: sum|w| * max|x| (the bound on any filtered value)."""
     return float(np.abs(dense_weights(w)).sum()) * float(vmax_abs)
+
+
+def brick_decompose(src: np.ndarray, brick, ghost: int = 0):
+    """BrickDecompose (Sec. 3.2, domain decomposition into subgrids with optional ghost
+    cells): the bricks of ``src`` (shape (nz, ny, nx)) for a brick size ``brick`` = (bx, by,
+    bz), in order (kz, ky, kx) with kx fastest.  Brick (kx, ky, kz) covers voxels [o, o + s),
+    o = k * b, s = min(b, n - o), and holds s + 2 ghost voxels per axis: voxel (i, j, k) is
+    src at clamp(o - ghost + (i, j, k)) per axis (clamp-to-edge beyond the faces)."""
+    nz, ny, nx = src.shape
+    bx, by, bz = brick
+    out = []
+    for oz in range(0, nz, bz):
+        for oy in range(0, ny, by):
+            for ox in range(0, nx, bx):
+                zi = np.clip(np.arange(oz - ghost, min(oz + bz, nz) + ghost), 0, nz - 1)
+                yi = np.clip(np.arange(oy - ghost, min(oy + by, ny) + ghost), 0, ny - 1)
+                xi = np.clip(np.arange(ox - ghost, min(ox + bx, nx) + ghost), 0, nx - 1)
+                out.append(src[np.ix_(zi, yi, xi)])
+    return out

@@ -345,6 +345,39 @@ def apply_filter_backward(grad_src, grad_weights, grad_dst: StructuredVolume,
               "vktApplyFilterBackwardSV")
 
 
+def brick_counts(src: StructuredVolume, brick) -> tuple:
+    """(countX, countY, countZ) of vktBrickDecomposeCountSV for brick = (bx, by, bz)."""
+    c = [ctypes.c_int32() for _ in range(3)]
+    check(_lib.vktBrickDecomposeCountSV(*(ctypes.byref(x) for x in c), src.handle, *map(int, brick)),
+          "vktBrickDecomposeCountSV")
+    return tuple(x.value for x in c)
+
+
+def brick_decompose(src_t, brick, ghost: int = 0, src_range=(0.0, 1.0), stream=None):
+    """BrickDecompose of a (nz, ny, nx) CUDA tensor: allocates the bricks as tensors of the
+    source dtype and fills them with vktBrickDecomposeSV.  Returns them in the order
+    (kz, ky, kx), kx fastest."""
+    torch = _torch()
+    src = StructuredVolume.from_tensor(src_t, *src_range)
+    cx, cy, cz = brick_counts(src, brick)
+    nz, ny, nx = src_t.shape
+    bx, by, bz = map(int, brick)
+    tensors, views = [], []
+    for kz in range(cz):
+        for ky in range(cy):
+            for kx in range(cx):
+                shape = (min(bz, nz - kz * bz) + 2 * ghost, min(by, ny - ky * by) + 2 * ghost,
+                         min(bx, nx - kx * bx) + 2 * ghost)
+                t = torch.empty(shape, dtype=src_t.dtype, device=src_t.device)
+                tensors.append(t)
+                views.append(StructuredVolume.from_tensor(t, *src_range))
+    arr = (ctypes.c_void_p * len(views))(*(v.handle.value for v in views))
+    with policy(stream=stream):
+        check(_lib.vktBrickDecomposeSV(arr, len(views), src.handle, bx, by, bz, int(ghost)),
+              "vktBrickDecomposeSV")
+    return tensors
+
+
 def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
                   dst_range=(0.0, 1.0), path=None, out=None, roi=None):
     """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor (roi:

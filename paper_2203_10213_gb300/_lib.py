@@ -58,6 +58,8 @@ SIGNATURES = {
     "vktFilterDestroy": [p],
     "vktApplyFilterSV": [p, p, p],
     "vktApplyFilterRangeSV": [p, p, p, i32, i32, i32, i32, i32, i32],
+    "vktBrickDecomposeCountSV": [pi32, pi32, pi32, p, i32, i32, i32],
+    "vktBrickDecomposeSV": [ctypes.POINTER(ctypes.c_void_p), i32, p, i32, i32, i32, i32],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],

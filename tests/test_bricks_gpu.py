@@ -1,0 +1,64 @@
+"""GPU parity of BrickDecompose (vktBrickDecomposeSV): every brick, ghost cells included,
+bit-exact against the oracle's decomposition, for every storage format, brick sizes that do
+and do not divide the volume (and exceed it), and ghost widths 0 to beyond a brick."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2203_10213_gb300 as vkt  # noqa: E402
+
+SEED = synth.BASE_SEED + 800
+
+
+def volume(fmt, shape, seed):
+    if fmt == synth.F32:
+        return synth.uniform(seed, shape, -3.0, 3.0)
+    return synth.quantize(synth.uniform(seed, shape), fmt)
+
+
+@pytest.mark.parametrize("fmt", [synth.U8, synth.U16, synth.F32])
+@pytest.mark.parametrize("shape,brick,ghost", [
+    ((40, 37, 70), (16, 16, 16), 0),
+    ((40, 37, 70), (16, 16, 16), 2),
+    ((33, 20, 65), (64, 8, 11), 3),      # x brick wider than the volume
+    ((9, 10, 11), (4, 3, 2), 5),         # ghost wider than a brick
+    ((1, 1, 1), (1, 1, 1), 1),
+])
+def test_bricks_match_oracle(fmt, shape, brick, ghost):
+    src = volume(fmt, shape, SEED + sum(shape) + ghost)
+    got = vkt.brick_decompose(torch.from_numpy(src).cuda(), brick, ghost)
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    ref = oracle.brick_decompose(src, brick, ghost)
+    assert len(got) == len(ref)
+    for i, (g, r) in enumerate(zip(got, ref)):
+        g = g.cpu().numpy()
+        assert g.shape == r.shape, i
+        assert np.array_equal(g.view(np.uint8), np.ascontiguousarray(r).view(np.uint8)), f"brick {i}"
+
+
+def test_bricks_of_the_512_volume_reassemble_it():
+    """The 512^3 uint8 CT-like volume in 64^3 bricks with 2 ghost cells (the halo a 5^3
+    filter needs): interiors reassemble the volume, ghosts match their neighbours."""
+    src = synth.volume("blobs", synth.U8, (512, 512, 512), synth.BASE_SEED + 1)
+    s = torch.from_numpy(src).cuda()
+    g = 2
+    bricks = vkt.brick_decompose(s, (64, 64, 64), g)
+    torch.cuda.synchronize()
+    assert len(bricks) == 512
+    inner = torch.empty_like(s)
+    for i, b in enumerate(bricks):
+        kz, ky, kx = i // 64, (i // 8) % 8, i % 8
+        inner[kz * 64:(kz + 1) * 64, ky * 64:(ky + 1) * 64, kx * 64:(kx + 1) * 64] = b[g:-g, g:-g, g:-g]
+    assert torch.equal(inner, s)
+    # ghosts of an interior brick are the neighbouring voxels of the volume
+    b = bricks[(3 * 8 + 4) * 8 + 5]
+    assert torch.equal(b, s[3 * 64 - g:4 * 64 + g, 4 * 64 - g:5 * 64 + g, 5 * 64 - g:6 * 64 + g])

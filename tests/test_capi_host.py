@@ -123,6 +123,36 @@ def test_apply_filter_range_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+def test_brick_decompose_validation_without_device(vkt, lib):
+    src = ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(src), ctypes.c_void_p(0x100000), 10, 7, 5,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    cx, cy, cz = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    C = lib.vktBrickDecomposeCountSV
+    assert C(ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(cz), src, 4, 7, 2) == 0
+    assert (cx.value, cy.value, cz.value) == (3, 1, 3)
+    assert C(ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(cz), src, 0, 7, 2) == 1
+    assert C(ctypes.byref(cx), ctypes.byref(cy), ctypes.byref(cz), None, 4, 7, 2) == 2
+    # one brick of the whole volume with ghost 1: dims 12 x 9 x 7
+    good, wrong_dims, wrong_fmt = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(good), ctypes.c_void_p(0x200000), 12, 9, 7,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(wrong_dims), ctypes.c_void_p(0x300000), 12, 9, 8,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(wrong_fmt), ctypes.c_void_p(0x400000), 12, 9, 7,
+                                             vkt.F32, 1, 1, 1, 0, 1) == 0
+    D = lib.vktBrickDecomposeSV
+    arr = lambda *h: (ctypes.c_void_p * len(h))(*(x.value for x in h))
+    assert D(arr(good), 1, src, 10, 7, 5, -1) == 1          # negative ghost
+    assert D(arr(good), 2, src, 10, 7, 5, 1) == 1           # count mismatch
+    assert D(arr(wrong_dims), 1, src, 10, 7, 5, 1) == 3     # brick dims
+    assert D(arr(wrong_fmt), 1, src, 10, 7, 5, 1) == 1      # brick format
+    assert D(arr(src), 1, src, 10, 7, 5, 0) == 1            # the source itself (overlap)
+    assert D(arr(good), 1, src, 10, 7, 5, 1) == 6           # valid: reaches the device check
+    for h in (src, good, wrong_dims, wrong_fmt):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
 def test_owning_create_reports_missing_device(vkt, lib):
     import torch
     if torch.cuda.is_available():

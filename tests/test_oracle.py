@@ -347,3 +347,63 @@ def test_planted_zero_padding_is_caught():
     w = rnd_w(91, 3)
     wrong = ndimage.correlate(x.astype(np.float64), w, mode="constant")
     assert np.max(np.abs(oracle.correlate(x, w) - wrong)) > 1e-3
+
+
+# ---------------------------------------------------------------------- BrickDecompose
+
+BRICK_CASES = [((7, 5, 6), (3, 2, 4), 0), ((7, 5, 6), (3, 2, 4), 1), ((9, 4, 5), (4, 4, 4), 2),
+               ((3, 3, 3), (8, 8, 8), 3), ((5, 6, 4), (1, 1, 1), 1)]
+
+
+def brick_origins(shape, brick):
+    nz, ny, nx = shape
+    bx, by, bz = brick
+    return [(ox, oy, oz) for oz in range(0, nz, bz) for oy in range(0, ny, by)
+            for ox in range(0, nx, bx)]
+
+
+@pytest.mark.parametrize("shape,brick,ghost", BRICK_CASES)
+def test_bricks_match_edge_padded_slices(shape, brick, ghost):
+    """Against numpy's own clamp-to-edge padding: brick = pad(src, ghost, 'edge') sliced at
+    the brick's origin with the brick's stored size."""
+    src = rnd_vol(100, shape)
+    pad = np.pad(src, ghost, mode="edge")
+    bricks = oracle.brick_decompose(src, brick, ghost)
+    origins = brick_origins(shape, brick)
+    assert len(bricks) == len(origins)
+    nz, ny, nx = shape
+    bx, by, bz = brick
+    for b, (ox, oy, oz) in zip(bricks, origins):
+        sx, sy, sz = min(bx, nx - ox), min(by, ny - oy), min(bz, nz - oz)
+        assert b.shape == (sz + 2 * ghost, sy + 2 * ghost, sx + 2 * ghost)
+        assert np.array_equal(b, pad[oz:oz + sz + 2 * ghost, oy:oy + sy + 2 * ghost,
+                                     ox:ox + sx + 2 * ghost])
+
+
+@pytest.mark.parametrize("shape,brick,ghost", BRICK_CASES)
+def test_brick_interiors_tile_the_volume(shape, brick, ghost):
+    """The interiors reassemble the volume exactly, each voxel once."""
+    src = rnd_vol(101, shape)
+    out = np.full(shape, np.nan)
+    g = ghost
+    for b, (ox, oy, oz) in zip(oracle.brick_decompose(src, brick, ghost), brick_origins(shape, brick)):
+        inner = b[g:b.shape[0] - g, g:b.shape[1] - g, g:b.shape[2] - g]
+        sl = (slice(oz, oz + inner.shape[0]), slice(oy, oy + inner.shape[1]), slice(ox, ox + inner.shape[2]))
+        assert np.isnan(out[sl]).all()
+        out[sl] = inner
+    assert np.array_equal(out, src)
+
+
+def test_brick_ghosts_hold_neighbours_and_repeat_faces():
+    src = rnd_vol(102, (6, 6, 8))
+    g = 2
+    bricks = oracle.brick_decompose(src, (4, 6, 6), g)     # two bricks along x
+    left, right = bricks
+    # the left brick's +x ghost columns are the right brick's first interior columns
+    assert np.array_equal(left[:, :, -g:], right[:, :, g:2 * g])
+    assert np.array_equal(right[:, :, :g], left[:, :, -2 * g:-g])
+    # beyond the -x face the ghosts repeat the face voxel; likewise in y and z
+    for c in range(g):
+        assert np.array_equal(left[:, :, c], left[:, :, g])
+        assert np.array_equal(left[:, c, :], left[:, g, :])
+        assert np.array_equal(left[c], left[g])

@@ -70,6 +70,8 @@ def _load():
             lib.oracle_backward_input_points.restype = i32
             lib.oracle_backward_input_points.argtypes = [p, i64, i64, i64, p, i32, p, i64, p]
             lib.oracle_num_threads.restype = i32
+            lib.oracle_clahe3d.restype = i32
+            lib.oracle_clahe3d.argtypes = [p, i64, i64, i64, i32, i32, i32, d, p, p, p]
             _lib = lib
     return _lib
 
@@ -231,3 +233,21 @@ def brick_decompose(src: np.ndarray, brick, ghost: int = 0):
                 xi = np.clip(np.arange(ox - ghost, min(ox + bx, nx) + ghost), 0, nx - 1)
                 out.append(src[np.ix_(zi, yi, xi)])
     return out
+
+
+def clahe3d(src: np.ndarray, bricks, clip: float):
+    """CLAHE-3D of a uint8 volume (Sec. 4.1 case study; the readings are listed in
+    oracle.c): returns (codes uint8, blended values float64 before rounding, per-brick
+    mappings uint8 of shape (nbz, nby, nbx, 256)).  bricks = (nbx, nby, nbz) bricks per axis,
+    dividing the dims."""
+    src = _c(src, np.uint8)
+    nz, ny, nx = src.shape
+    nbx, nby, nbz = (int(b) for b in bricks)
+    out = np.empty_like(src)
+    t = np.empty(src.shape, dtype=np.float64)
+    luts = np.empty((nbz, nby, nbx, 256), dtype=np.uint8)
+    rc = _load().oracle_clahe3d(_ptr(src), nx, ny, nz, nbx, nby, nbz, float(clip), _ptr(out),
+                                _ptr(t), _ptr(luts))
+    if rc != 0:
+        raise ValueError("oracle_clahe3d: bricks must divide the dims")
+    return out, t, luts

@@ -283,3 +283,113 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * CLAHE-3D (Sec. 4.1 "Case Study: CLAHE-3D": contrast limited adaptive histogram
+ * equalisation, a 3-D variant of the 2-D method; brick decomposition, local histograms, a
+ * maximum cut-off on the histograms, and linear interpolation of the local results).  The
+ * paper gives the steps but not their constants; the readings taken (uint8 volumes):
+ *   - bricks: nb = (nbx, nby, nbz) bricks per axis that divide the dims exactly; brick size
+ *     s = dims / nb, N = sx*sy*sz voxels per brick;
+ *   - histogram: 256 bins of the stored codes of each brick;
+ *   - clip: limit L = max(1, floor(clip * N / 256)) (clip <= 0: no clipping); the excess
+ *     E = sum max(h - L, 0) is removed and given back evenly, E / 256 to every bin, and the
+ *     remaining E mod 256 counts one each to bins 0, step, 2 step, ... with
+ *     step = max(1, 256 / (E mod 256)), while any remain;
+ *   - mapping of a brick: lut[q] = floor((255 * cdf[q] + N / 2) / N), cdf[q] = sum_{i<=q} h[i];
+ *   - interpolation: voxel x lies at brick coordinate t = (x + 0.5) / sx - 0.5 per axis;
+ *     b0 = floor(t), w = t - b0, b1 = b0 + 1, both clamped to [0, nb - 1]; the result is the
+ *     trilinear blend of the 8 bricks' lut[q] with weights (1 - w, w) per axis, rounded
+ *     half-to-even to a code.
+ * t_out receives the blended values before rounding (for the tie window of the tests).
+ */
+static void clahe_lut(const int64_t* hist_in, int64_t n, double clip, uint8_t* lut)
+{
+    int64_t h[256];
+    for (int i = 0; i < 256; ++i) h[i] = hist_in[i];
+    if (clip > 0.0) {
+        int64_t limit = (int64_t)floor(clip * (double)n / 256.0);
+        if (limit < 1) limit = 1;
+        int64_t excess = 0;
+        for (int i = 0; i < 256; ++i)
+            if (h[i] > limit) {
+                excess += h[i] - limit;
+                h[i] = limit;
+            }
+        const int64_t add = excess / 256;
+        int64_t rem = excess - add * 256;
+        for (int i = 0; i < 256; ++i) h[i] += add;
+        if (rem > 0) {
+            int64_t step = 256 / rem;
+            if (step < 1) step = 1;
+            for (int64_t i = 0; i < 256 && rem > 0; i += step) {
+                h[i] += 1;
+                rem -= 1;
+            }
+        }
+    }
+    int64_t cdf = 0;
+    for (int i = 0; i < 256; ++i) {
+        cdf += h[i];
+        int64_t v = (255 * cdf + n / 2) / n;
+        lut[i] = (uint8_t)(v > 255 ? 255 : v);
+    }
+}
+
+int oracle_clahe3d(const uint8_t* src, int64_t nx, int64_t ny, int64_t nz, int nbx, int nby,
+                   int nbz, double clip, uint8_t* out, double* t_out, uint8_t* luts_out)
+{
+    if (nbx < 1 || nby < 1 || nbz < 1) return -1;
+    if (nx % nbx || ny % nby || nz % nbz) return -1;
+    const int64_t sx = nx / nbx, sy = ny / nby, sz = nz / nbz, n = sx * sy * sz;
+    const int64_t nbricks = (int64_t)nbx * nby * nbz;
+    uint8_t* luts = (uint8_t*)malloc((size_t)nbricks * 256);
+    int64_t* hist = (int64_t*)calloc((size_t)nbricks * 256, sizeof(int64_t));
+    if (!luts || !hist) {
+        free(luts);
+        free(hist);
+        return -2;
+    }
+    /* local histograms */
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                const int64_t b = ((z / sz) * nby + (y / sy)) * nbx + (x / sx);
+                hist[b * 256 + src[(z * ny + y) * nx + x]] += 1;
+            }
+    /* clipped, redistributed, equalised mapping of every brick */
+    for (int64_t b = 0; b < nbricks; ++b) clahe_lut(hist + b * 256, n, clip, luts + b * 256);
+    /* trilinear blend of the 8 nearest bricks' mappings */
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < nz; ++z) {
+        const double tz = ((double)z + 0.5) / (double)sz - 0.5;
+        const double fz = floor(tz), wz = tz - fz;
+        const int64_t z0 = clampi((int64_t)fz, nbz), z1 = clampi((int64_t)fz + 1, nbz);
+        for (int64_t y = 0; y < ny; ++y) {
+            const double ty = ((double)y + 0.5) / (double)sy - 0.5;
+            const double fy = floor(ty), wy = ty - fy;
+            const int64_t y0 = clampi((int64_t)fy, nby), y1 = clampi((int64_t)fy + 1, nby);
+            for (int64_t x = 0; x < nx; ++x) {
+                const double tx = ((double)x + 0.5) / (double)sx - 0.5;
+                const double fx = floor(tx), wx = tx - fx;
+                const int64_t x0 = clampi((int64_t)fx, nbx), x1 = clampi((int64_t)fx + 1, nbx);
+                const int64_t i = (z * ny + y) * nx + x;
+                const int q = src[i];
+                double v = 0.0;
+                for (int c = 0; c < 8; ++c) {
+                    const int64_t bx = (c & 1) ? x1 : x0, by = (c & 2) ? y1 : y0, bz = (c & 4) ? z1 : z0;
+                    const double w = ((c & 1) ? wx : 1.0 - wx) * ((c & 2) ? wy : 1.0 - wy) *
+                                     ((c & 4) ? wz : 1.0 - wz);
+                    v += w * (double)luts[((bz * nby + by) * nbx + bx) * 256 + q];
+                }
+                if (t_out) t_out[i] = v;
+                double r = nearbyint(v);     /* round half to even (default rounding mode) */
+                out[i] = (uint8_t)(r < 0.0 ? 0.0 : (r > 255.0 ? 255.0 : r));
+            }
+        }
+    }
+    if (luts_out) memcpy(luts_out, luts, (size_t)nbricks * 256);
+    free(luts);
+    free(hist);
+    return 0;
+}

@@ -407,3 +407,71 @@ def test_brick_ghosts_hold_neighbours_and_repeat_faces():
         assert np.array_equal(left[:, :, c], left[:, :, g])
         assert np.array_equal(left[:, c, :], left[:, g, :])
         assert np.array_equal(left[c], left[g])
+
+
+# ---------------------------------------------------------------------- CLAHE-3D
+
+def u8_vol(seed, shape):
+    return synth.quantize(synth.uniform(seed, shape), synth.U8)
+
+
+def test_clahe_single_brick_without_clip_is_histogram_equalisation():
+    """One brick, no clip limit: the textbook global histogram equalisation of the codes."""
+    v = u8_vol(110, (10, 12, 14))
+    out, t, luts = oracle.clahe3d(v, (1, 1, 1), 0.0)
+    n = v.size
+    cdf = np.cumsum(np.bincount(v.ravel(), minlength=256))
+    lut = np.minimum((255 * cdf + n // 2) // n, 255)
+    assert np.array_equal(luts[0, 0, 0], lut)
+    assert np.array_equal(out, lut[v])
+
+
+@pytest.mark.parametrize("clip", [0.5, 1.0, 3.0, 40.0])
+def test_clahe_clip_conserves_counts_and_limits_contrast(clip):
+    v = synth.quantize(synth.blobs(111, (12, 12, 12), nblobs=3, sigma=(2.0, 5.0)), synth.U8)
+    n = v.size
+    _, _, luts = oracle.clahe3d(v, (1, 1, 1), clip)
+    lut = luts[0, 0, 0].astype(np.int64)
+    assert lut[255] == 255                      # the redistributed counts still sum to N
+    assert np.all(np.diff(lut) >= 0)            # a mapping that keeps the order of codes
+    limit = max(1, int(np.floor(clip * n / 256)))
+    # one code adds at most limit + ceil(excess/256) + 1 counts: its contrast is capped
+    cap = (limit + (n // 256) + 2) * 255 / n + 1
+    assert np.max(np.diff(lut)) <= cap
+
+
+def test_clahe_brick_centres_take_their_own_mapping():
+    """With odd brick sizes a voxel at a brick centre has interpolation weights 0/1, so it
+    maps through its own brick's mapping exactly."""
+    v = u8_vol(112, (10, 15, 20))             # bricks 5 x 5 x 5 for nb = (4, 3, 2)
+    out, _, luts = oracle.clahe3d(v, (4, 3, 2), 2.0)
+    for bz in range(2):
+        for by in range(3):
+            for bx in range(4):
+                x, y, z = 5 * bx + 2, 5 * by + 2, 5 * bz + 2
+                assert out[z, y, x] == luts[bz, by, bx, v[z, y, x]]
+
+
+def test_clahe_blend_is_scipy_trilinear_interpolation():
+    """Between the centres the result is the linear interpolation (edge-clamped) of the
+    bricks' mappings at the voxel's brick coordinate, as scipy's map_coordinates computes."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    v = u8_vol(113, (8, 12, 16))
+    nb = (4, 3, 2)
+    _, t, luts = oracle.clahe3d(v, nb, 1.5)
+    nz, ny, nx = v.shape
+    s = (nx // nb[0], ny // nb[1], nz // nb[2])
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    coords = [(zz + 0.5) / s[2] - 0.5, (yy + 0.5) / s[1] - 0.5, (xx + 0.5) / s[0] - 0.5]
+    ref = np.empty(v.shape)
+    for q in np.unique(v):
+        m = v == q
+        grid = luts[..., q].astype(np.float64)
+        ref[m] = ndimage.map_coordinates(grid, [c[m] for c in coords], order=1, mode="nearest")
+    assert np.max(np.abs(ref - t)) < 1e-9
+
+
+def test_clahe_constant_volume_stays_constant():
+    v = np.full((8, 8, 8), 77, dtype=np.uint8)
+    out, _, _ = oracle.clahe3d(v, (2, 2, 2), 2.0)
+    assert np.all(out == out[0, 0, 0])

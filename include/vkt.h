@@ -322,6 +322,27 @@ VKT_API vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBri
                                      vktStructuredVolume volume, int32_t brickX, int32_t brickY,
                                      int32_t brickZ, int32_t ghost);
 
+/* ------------------------------------------------------------------ CLAHE-3D */
+
+/*
+ * CLAHE-3D (Sec. 4.1, "Case Study: CLAHE-3D": contrast limited adaptive histogram
+ * equalisation by brick decomposition, local histograms with a maximum cut-off, and linear
+ * interpolation of the local results).  uint8 volumes only (else UNSUPPORTED); dst and src
+ * have equal dims (else DIMS_MISMATCH) and do not overlap (else INVALID_VALUE).  The volume
+ * is split into bricksX x bricksY x bricksZ bricks, which must divide the dims (else
+ * INVALID_VALUE); N = voxels per brick.  Per brick: a 256-bin histogram of the codes; with
+ * clipLimit > 0 every bin is cut at L = max(1, floor(clipLimit * N / 256)) and the excess E
+ * is handed back, E / 256 to every bin and the remaining E mod 256 one each to bins 0,
+ * step, 2 step, ... (step = max(1, 256 / (E mod 256))); clipLimit <= 0 disables the cut;
+ * the brick's mapping is lut[q] = floor((255 * cdf[q] + N/2) / N).  Each voxel's code q is
+ * then mapped by the trilinear blend of the 8 nearest bricks' lut[q], the voxel at brick
+ * coordinate t = (x + 0.5) / s - 0.5 per axis (clamped to the brick grid), rounded half
+ * to even.  Stored codes are used as they are (the value range plays no part).
+ * Asynchronous on the policy stream; histograms and mappings use stream-ordered scratch.
+ */
+VKT_API vktError vktClahe3DSV(vktStructuredVolume dst, vktStructuredVolume src, int32_t bricksX,
+                              int32_t bricksY, int32_t bricksZ, float clipLimit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -378,6 +378,20 @@ def brick_decompose(src_t, brick, ghost: int = 0, src_range=(0.0, 1.0), stream=N
     return tensors
 
 
+def clahe3d(src_t, bricks, clip_limit: float, out=None, stream=None):
+    """CLAHE-3D of a (nz, ny, nx) uint8 CUDA tensor (vktClahe3DSV); bricks = (bx, by, bz)
+    bricks per axis dividing the dims.  Returns the uint8 result tensor."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(src_t)
+    src = StructuredVolume.from_tensor(src_t)
+    dst = StructuredVolume.from_tensor(out)
+    with policy(stream=stream):
+        check(_lib.vktClahe3DSV(dst.handle, src.handle, *map(int, bricks), float(clip_limit)),
+              "vktClahe3DSV")
+    return out
+
+
 def filter_tensor(src_t, filt: Filter, dst_dtype=None, src_range=(0.0, 1.0),
                   dst_range=(0.0, 1.0), path=None, out=None, roi=None):
     """Convenience: filters a (nz, ny, nx) CUDA tensor and returns the result tensor (roi:

@@ -60,6 +60,7 @@ SIGNATURES = {
     "vktApplyFilterRangeSV": [p, p, p, i32, i32, i32, i32, i32, i32],
     "vktBrickDecomposeCountSV": [pi32, pi32, pi32, p, i32, i32, i32],
     "vktBrickDecomposeSV": [ctypes.POINTER(ctypes.c_void_p), i32, p, i32, i32, i32, i32],
+    "vktClahe3DSV": [p, p, i32, i32, i32, ctypes.c_float],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],

@@ -153,6 +153,25 @@ def test_brick_decompose_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+def test_clahe_validation_without_device(vkt, lib):
+    a, b, f = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(a), ctypes.c_void_p(0x100000), 16, 8, 4,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(b), ctypes.c_void_p(0x200000), 16, 8, 4,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(f), ctypes.c_void_p(0x300000), 16, 8, 4,
+                                             vkt.F32, 1, 1, 1, 0, 1) == 0
+    C = lib.vktClahe3DSV
+    assert C(None, a, 2, 2, 2, 2.0) == 2
+    assert C(f, a, 2, 2, 2, 2.0) == 4            # not uint8
+    assert C(b, a, 3, 2, 2, 2.0) == 1            # 3 does not divide 16
+    assert C(b, a, 2, 0, 2, 2.0) == 1
+    assert C(a, a, 2, 2, 2, 2.0) == 1            # overlapping
+    assert C(b, a, 4, 4, 2, 2.0) == 6            # valid: reaches the device check
+    for h in (a, b, f):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
 def test_owning_create_reports_missing_device(vkt, lib):
     import torch
     if torch.cuda.is_available():

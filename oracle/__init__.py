@@ -70,6 +70,9 @@ def _load():
             lib.oracle_backward_input_points.restype = i32
             lib.oracle_backward_input_points.argtypes = [p, i64, i64, i64, p, i32, p, i64, p]
             lib.oracle_num_threads.restype = i32
+            lib.oracle_render.restype = i32
+            lib.oracle_render.argtypes = [p, i32, d, d, i64, i64, i64, i32, i32, p, p, p, d, d, d,
+                                          p, i32, p, p]
             lib.oracle_clahe3d.restype = i32
             lib.oracle_clahe3d.argtypes = [p, i64, i64, i64, i32, i32, i32, d, p, p, p]
             _lib = lib
@@ -251,3 +254,22 @@ def clahe3d(src: np.ndarray, bricks, clip: float):
     if rc != 0:
         raise ValueError("oracle_clahe3d: bricks must divide the dims")
     return out, t, luts
+
+
+def render(src: np.ndarray, lo: float, hi: float, width: int, height: int, eye, center, up,
+           fovy: float, step: float, termination: float, background, lut):
+    """Headless ray marching with absorption and emission (Sec. 3.2 Render; readings in
+    oracle.c): an (height, width, 4) float64 RGBA image.  lut: (n, 4) straight RGBA."""
+    src = np.ascontiguousarray(src)
+    fmt = _fmt_of(src)
+    nz, ny, nx = src.shape
+    lut = _c(lut, np.float64).reshape(-1, 4)
+    out = np.empty((height, width, 4), dtype=np.float64)
+    vec = lambda v: _c(v, np.float64).reshape(-1)
+    e, c, u, bg = vec(eye), vec(center), vec(up), vec(background)
+    rc = _load().oracle_render(_ptr(src), fmt, float(lo), float(hi), nx, ny, nz, int(width),
+                               int(height), _ptr(e), _ptr(c), _ptr(u), float(fovy), float(step),
+                               float(termination), _ptr(bg), lut.shape[0], _ptr(lut), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_render: bad arguments")
+    return out

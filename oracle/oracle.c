@@ -393,3 +393,119 @@ int oracle_clahe3d(const uint8_t* src, int64_t nx, int64_t ny, int64_t nz, int n
     free(hist);
     return 0;
 }
+
+/*
+ * Headless Render, ray marching with absorption and emission (Sec. 3.2 "Rendering": the
+ * Render algorithm's volume ray marching with absorption and emission, classified by an
+ * RGBA lookup table).  No window: one RGBA value per pixel.  Readings (the paper gives
+ * none of these):
+ *   - world = voxel units, the volume is the box [0,nx] x [0,ny] x [0,nz], voxel (i,j,k)
+ *     centred at (i+0.5, j+0.5, k+0.5); a sample's value is the trilinear blend of the
+ *     mapped voxel values at p - 0.5 (indices clamped to the volume);
+ *   - classification: u = clamp((v - lo) / (hi - lo), 0, 1); the table's n entries sit at
+ *     u = i / (n-1) and are blended linearly; colours are straight (not premultiplied),
+ *     alpha is the opacity of one voxel length and is corrected to the step:
+ *     a' = 1 - (1 - a)^step;
+ *   - camera: pinhole at eye looking at center, vertical field of view fovy, up vector;
+ *     pixel (px, py) (py = 0 at the top) looks along
+ *       normalize(f + (2(px+0.5)/W - 1) tan(fovy/2) (W/H) r + (1 - 2(py+0.5)/H) tan(fovy/2) u),
+ *     f = normalize(center - eye), r = normalize(f x up), u = r x f;
+ *   - the ray enters the box at t0 = max(tnear, 0), leaves at t1 (slab test; an axis with a
+ *     direction component below 1e-12 in magnitude is parallel: the ray misses the box if it
+ *     lies outside that slab); samples at t0 + (k + 0.5) step while below t1;
+ *   - front-to-back compositing: C += (1 - A) a' c, A += (1 - A) a'; marching stops after a
+ *     sample that brings A to `termination` or above;
+ *   - pixel = (C + (1 - A) bg.rgb, A + (1 - A) bg.a).
+ */
+static double sample_trilinear(const void* src, int fmt, double lo, double hi, int64_t nx,
+                               int64_t ny, int64_t nz, double px, double py, double pz)
+{
+    const double x = px - 0.5, y = py - 0.5, z = pz - 0.5;
+    const double fx = floor(x), fy = floor(y), fz = floor(z);
+    const double wx = x - fx, wy = y - fy, wz = z - fz;
+    const int64_t ix = (int64_t)fx, iy = (int64_t)fy, iz = (int64_t)fz;
+    double v = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        const int64_t i = clampi(ix + (c & 1), nx), j = clampi(iy + ((c >> 1) & 1), ny),
+                      k = clampi(iz + ((c >> 2) & 1), nz);
+        const double w = ((c & 1) ? wx : 1.0 - wx) * (((c >> 1) & 1) ? wy : 1.0 - wy) *
+                         (((c >> 2) & 1) ? wz : 1.0 - wz);
+        v += w * mapped(src, fmt, (k * ny + j) * nx + i, lo, hi);
+    }
+    return v;
+}
+
+static void normalize3(double* v)
+{
+    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    v[0] /= n;
+    v[1] /= n;
+    v[2] /= n;
+}
+
+int oracle_render(const void* src, int fmt, double lo, double hi, int64_t nx, int64_t ny,
+                  int64_t nz, int width, int height, const double* eye, const double* center,
+                  const double* up, double fovy, double step, double termination,
+                  const double* bg, int lut_n, const double* lut, double* rgba)
+{
+    if (width < 1 || height < 1 || lut_n < 2 || !(step > 0.0)) return -1;
+    double f[3] = {center[0] - eye[0], center[1] - eye[1], center[2] - eye[2]};
+    normalize3(f);
+    double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    normalize3(r);
+    const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+    const double th = tan(0.5 * fovy), aspect = (double)width / (double)height;
+    const double box[3] = {(double)nx, (double)ny, (double)nz};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int py = 0; py < height; ++py)
+        for (int px = 0; px < width; ++px) {
+            const double sx = (2.0 * (px + 0.5) / width - 1.0) * th * aspect;
+            const double sy = (1.0 - 2.0 * (py + 0.5) / height) * th;
+            double d[3] = {f[0] + sx * r[0] + sy * u[0], f[1] + sx * r[1] + sy * u[1],
+                           f[2] + sx * r[2] + sy * u[2]};
+            normalize3(d);
+            double tn = -INFINITY, tf = INFINITY;
+            int hit = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (fabs(d[a]) < 1e-12) {
+                    if (eye[a] < 0.0 || eye[a] > box[a]) hit = 0;
+                    continue;
+                }
+                double ta = (0.0 - eye[a]) / d[a], tb = (box[a] - eye[a]) / d[a];
+                if (ta > tb) {
+                    const double t = ta;
+                    ta = tb;
+                    tb = t;
+                }
+                if (ta > tn) tn = ta;
+                if (tb < tf) tf = tb;
+            }
+            const double t0 = tn > 0.0 ? tn : 0.0, t1 = tf;
+            double C[3] = {0.0, 0.0, 0.0}, A = 0.0;
+            if (hit && t0 < t1) {
+                for (int64_t k = 0;; ++k) {
+                    const double t = t0 + ((double)k + 0.5) * step;
+                    if (!(t < t1)) break;
+                    const double v = sample_trilinear(src, fmt, lo, hi, nx, ny, nz, eye[0] + t * d[0],
+                                                      eye[1] + t * d[1], eye[2] + t * d[2]);
+                    double un = (v - lo) / (hi - lo);
+                    un = un < 0.0 ? 0.0 : (un > 1.0 ? 1.0 : un);
+                    const double fi = un * (lut_n - 1);
+                    int i0 = (int)floor(fi);
+                    if (i0 > lut_n - 2) i0 = lut_n - 2;
+                    const double w = fi - i0;
+                    double c[4];
+                    for (int ch = 0; ch < 4; ++ch)
+                        c[ch] = (1.0 - w) * lut[4 * i0 + ch] + w * lut[4 * (i0 + 1) + ch];
+                    const double ac = 1.0 - pow(1.0 - c[3], step);
+                    for (int ch = 0; ch < 3; ++ch) C[ch] += (1.0 - A) * ac * c[ch];
+                    A += (1.0 - A) * ac;
+                    if (A >= termination) break;
+                }
+            }
+            double* o = rgba + 4 * ((int64_t)py * width + px);
+            for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + (1.0 - A) * bg[ch];
+            o[3] = A + (1.0 - A) * bg[3];
+        }
+    return 0;
+}

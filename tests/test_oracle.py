@@ -475,3 +475,69 @@ def test_clahe_constant_volume_stays_constant():
     v = np.full((8, 8, 8), 77, dtype=np.uint8)
     out, _, _ = oracle.clahe3d(v, (2, 2, 2), 2.0)
     assert np.all(out == out[0, 0, 0])
+
+
+# ---------------------------------------------------------------------- headless Render
+
+def render_uniform(value, lut, step=0.5, termination=2.0, size=(16, 12), eye=(4, 4, -20)):
+    v = np.full((8, 8, 8), value, np.float32)
+    return oracle.render(v, 0.0, 1.0, size[0], size[1], eye, (4, 4, 4), (0, 1, 0), 0.5, step,
+                         termination, (0.1, 0.2, 0.3, 0.4), lut)
+
+
+def test_render_transparent_volume_shows_the_background():
+    img = render_uniform(0.5, [[1, 1, 1, 0], [1, 1, 1, 0]])
+    assert np.allclose(img, np.array([0.1, 0.2, 0.3, 0.4]), atol=0, rtol=0)
+
+
+@pytest.mark.parametrize("step", [0.5, 0.25, 1.0])
+def test_render_uniform_slab_follows_beer_lambert(step):
+    """The centre ray crosses 8 voxel lengths of a uniform medium of per-voxel opacity a:
+    accumulated opacity 1 - (1 - a)^8 for any step dividing the path, colour c times it,
+    then the background behind."""
+    a = 0.1
+    # pixel (7, 5) of a 15 x 11 image looks along the axis, through z = 0 .. 8
+    img = render_uniform(0.5, [[0.8, 0.4, 0.2, a], [0.8, 0.4, 0.2, a]], step=step, size=(15, 11))
+    A = 1 - (1 - a) ** 8
+    px = img[5, 7]
+    assert abs(px[3] - (A + (1 - A) * 0.4)) < 1e-12
+    assert np.allclose(px[:3], np.array([0.8, 0.4, 0.2]) * A + (1 - A) * np.array([0.1, 0.2, 0.3]), atol=1e-12)
+
+
+def test_render_stops_at_the_termination_opacity():
+    a, step = 0.1, 0.5
+    img = render_uniform(0.5, [[1, 1, 1, a], [1, 1, 1, a]], step=step, termination=0.3, size=(15, 11))
+    ac = 1 - (1 - a) ** step
+    k = int(np.ceil(np.log(1 - 0.3) / np.log(1 - ac)))
+    A = 1 - (1 - ac) ** k
+    assert abs(img[5, 7, 3] - (A + (1 - A) * 0.4)) < 1e-12
+
+
+def test_render_table_is_blended_linearly():
+    """Value 0.25 between two table entries: colour 0.75 c0 + 0.25 c1."""
+    lut = [[1.0, 0.0, 0.0, 0.5], [0.0, 0.0, 1.0, 0.5]]
+    img = render_uniform(0.25, lut, size=(15, 11))
+    A = 1 - 0.5 ** 8
+    px = img[5, 7]
+    assert np.allclose(px[:3], np.array([0.75, 0.0, 0.25]) * A + (1 - A) * np.array([0.1, 0.2, 0.3]), atol=1e-12)
+
+
+def test_render_camera_orientation():
+    """Looking along +z with +y up, the right edge of the image is towards -x: an opaque
+    slab at low x appears in the right half, one at high y in the top half."""
+    v = np.zeros((8, 8, 8), np.float32)
+    v[:, :, :3] = 1.0                     # low x
+    lut = [[0, 0, 0, 0], [1, 1, 1, 1]]
+    img = oracle.render(v, 0.0, 1.0, 31, 31, (4, 4, -20), (4, 4, 4), (0, 1, 0), 0.5, 0.25, 2.0,
+                        (0, 0, 0, 0), lut)
+    assert img[15, 25, 3] > 0.5 and img[15, 5, 3] < 0.5
+    v = np.zeros((8, 8, 8), np.float32)
+    v[:, 5:, :] = 1.0                     # high y
+    img = oracle.render(v, 0.0, 1.0, 31, 31, (4, 4, -20), (4, 4, 4), (0, 1, 0), 0.5, 0.25, 2.0,
+                        (0, 0, 0, 0), lut)
+    assert img[5, 15, 3] > 0.5 and img[25, 15, 3] < 0.5
+
+
+def test_render_miss_rays_see_background():
+    img = render_uniform(0.5, [[1, 1, 1, 1], [1, 1, 1, 1]], size=(64, 48))
+    assert np.allclose(img[0, 0], [0.1, 0.2, 0.3, 0.4])

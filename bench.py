@@ -436,6 +436,51 @@ def clahe_form(vkt, torch, stream):
             "paper_context": "about 30 ms on a Quadro RTX 8000 (Sec. 4.1), other hardware"}
 
 
+# ------------------------------------------------------------------ render form
+
+def render_form(vkt, torch, stream, src):
+    """Headless ray marching (absorption and emission) of the step's 512^3 uint8 volume into
+    a 1024 x 768 RGBA float image, step 0.5 voxel, a four-entry ramp table, no early
+    termination: ms per frame, rays and samples per second (the samples counted on the host
+    from each pixel's ray-box interval)."""
+    import math
+    W, H, step = 1024, 768, 0.5
+    eye, center, up, fovy = (256.0, 300.0, -600.0), (256.0, 256.0, 256.0), (0.0, 1.0, 0.0), 0.8
+    lut = np.array([[0, 0, 0, 0], [0.9, 0.5, 0.2, 0.02], [1, 0.9, 0.6, 0.15], [1, 1, 1, 0.6]], np.float32)
+    img = vkt.render(src, W, H, eye, center, up, fovy, step, lut, stream=stream)
+    reps = 10
+    for _ in range(2):
+        vkt.render(src, W, H, eye, center, up, fovy, step, lut, out=img, stream=stream)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        vkt.render(src, W, H, eye, center, up, fovy, step, lut, out=img, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    ms = a.elapsed_time(b) / reps
+    # samples per ray from the same camera model (float64 on the host)
+    f = np.subtract(center, eye); f /= np.linalg.norm(f)
+    r = np.cross(f, up); r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    th = math.tan(fovy / 2)
+    px, py = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    d = (f[None, None] + ((2 * px / W - 1) * th * W / H)[..., None] * r
+         + ((1 - 2 * py / H) * th)[..., None] * u)
+    d /= np.linalg.norm(d, axis=-1, keepdims=True)
+    n = np.array(src.shape[::-1], dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ta = (0 - np.array(eye)) / d
+        tb = (n - np.array(eye)) / d
+    t0 = np.maximum(np.max(np.minimum(ta, tb), axis=-1), 0)
+    t1 = np.min(np.maximum(ta, tb), axis=-1)
+    samples = float(np.sum(np.where(t1 > t0, np.ceil((t1 - t0) / step - 0.5), 0)))
+    return {"image": [W, H], "step": step, "ms": round(ms, 4),
+            "mrays_s": round(W * H / (ms * 1e-3) / 1e6, 1),
+            "gsamples_s": round(samples / (ms * 1e-3) / 1e9, 2), "samples": int(samples)}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -590,6 +635,7 @@ def run_ours(args):
         bform = batching_form(args, vkt, torch, dev, stream)
     kform = brick_form(vkt, torch, stream, src)
     cform = clahe_form(vkt, torch, stream)
+    vform = render_form(vkt, torch, stream, src)
     g_roi = vkt.Filter.gaussian(5, 1.5)
     rform = range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g_roi, lap)
     g_roi.destroy()
@@ -605,7 +651,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "precision_form": pform, "batching_form": bform,
-            "range_form": rform, "brick_form": kform, "clahe_form": cform,
+            "range_form": rform, "brick_form": kform, "clahe_form": cform, "render_form": vform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

@@ -322,6 +322,54 @@ VKT_API vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBri
                                      vktStructuredVolume volume, int32_t brickX, int32_t brickY,
                                      int32_t brickZ, int32_t ghost);
 
+/* ------------------------------------------------------------------ Render (headless) */
+
+#define VKT_RENDER_MAX_LUT 256
+
+/*
+ * Parameters of vktRenderSV.  World coordinates are voxel units: the volume is the box
+ * [0,dx] x [0,dy] x [0,dz], voxel (i,j,k) centred at (i+0.5, j+0.5, k+0.5).
+ *   eye, center, up  pinhole camera at eye looking at center; up fixes the roll (must not be
+ *                    parallel to center - eye)
+ *   fovy             vertical field of view in radians, in (0, pi)
+ *   step             sample spacing along a ray in voxel lengths, > 0
+ *   termination      a ray stops once its accumulated opacity reaches this (> 1: never)
+ *   background       RGBA behind the volume
+ *   lutSize, lut     transfer function: lutSize (2 .. VKT_RENDER_MAX_LUT) straight RGBA
+ *                    entries in host memory, entry i at normalised value i / (lutSize - 1);
+ *                    alpha is the opacity of one voxel length
+ */
+typedef struct vktRenderParams {
+    float eye[3];
+    float center[3];
+    float up[3];
+    float fovy;
+    float step;
+    float termination;
+    float background[4];
+    int32_t lutSize;
+    const float* lut;
+} vktRenderParams;
+
+/*
+ * Headless Render (Sec. 3.2 "Rendering": volume ray marching with absorption and emission,
+ * samples classified by an RGBA lookup table), without a window: rgba receives
+ * height x width RGBA float pixels (device memory, 16-byte aligned, row 0 at the top).
+ * Pixel (px, py) casts the ray through its centre,
+ *   normalize(f + (2(px+0.5)/width - 1) tan(fovy/2) (width/height) r + (1 - 2(py+0.5)/height) tan(fovy/2) u),
+ * f = normalize(center - eye), r = normalize(f x up), u = r x f.  The ray enters the box at
+ * t0 = max(t_near, 0) and is sampled at t0 + (k + 0.5) step while inside.  A sample's value is
+ * the trilinear blend of the mapped voxel values (clamped at the faces), normalised to
+ * u = clamp((v - lo) / (hi - lo), 0, 1) by the volume's range and classified by the linearly
+ * blended table entry; its opacity is corrected to the step, a' = 1 - (1 - a)^step, and it is
+ * composited front to back (C += (1 - A) a' c, A += (1 - A) a').  The pixel is
+ * (C + (1 - A) background.rgb, A + (1 - A) background.a).  INVALID_VALUE for bad parameters
+ * (sizes, table, step, field of view, camera, an empty value range).  Asynchronous on the
+ * policy stream; the table is copied at the call.
+ */
+VKT_API vktError vktRenderSV(float* rgba, int32_t width, int32_t height, vktStructuredVolume volume,
+                             const vktRenderParams* params);
+
 /* ------------------------------------------------------------------ CLAHE-3D */
 
 /*

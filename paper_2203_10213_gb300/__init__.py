@@ -378,6 +378,38 @@ def brick_decompose(src_t, brick, ghost: int = 0, src_range=(0.0, 1.0), stream=N
     return tensors
 
 
+class RenderParams(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("center", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fovy", ctypes.c_float), ("step", ctypes.c_float), ("termination", ctypes.c_float),
+                ("background", ctypes.c_float * 4), ("lutSize", ctypes.c_int32),
+                ("lut", ctypes.POINTER(ctypes.c_float))]
+
+
+def render(src_t, width: int, height: int, eye, center, up, fovy: float, step: float, lut,
+           termination: float = 2.0, background=(0.0, 0.0, 0.0, 0.0), src_range=(0.0, 1.0),
+           out=None, stream=None):
+    """Headless ray marching of a (nz, ny, nx) CUDA volume tensor (vktRenderSV): returns an
+    (height, width, 4) float32 CUDA tensor.  lut: (n, 4) straight RGBA transfer function."""
+    import numpy as _np
+    torch = _torch()
+    table = _np.ascontiguousarray(_np.asarray(lut, dtype=_np.float32).reshape(-1, 4))
+    if out is None:
+        out = torch.empty((height, width, 4), dtype=torch.float32, device=src_t.device)
+    vol = StructuredVolume.from_tensor(src_t, *src_range)
+    prm = RenderParams()
+    prm.eye[:] = [float(x) for x in eye]
+    prm.center[:] = [float(x) for x in center]
+    prm.up[:] = [float(x) for x in up]
+    prm.fovy, prm.step, prm.termination = float(fovy), float(step), float(termination)
+    prm.background[:] = [float(x) for x in background]
+    prm.lutSize = table.shape[0]
+    prm.lut = table.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    with policy(stream=stream):
+        check(_lib.vktRenderSV(ctypes.c_void_p(out.data_ptr()), int(width), int(height), vol.handle,
+                               ctypes.cast(ctypes.pointer(prm), ctypes.c_void_p)), "vktRenderSV")
+    return out
+
+
 def clahe3d(src_t, bricks, clip_limit: float, out=None, stream=None):
     """CLAHE-3D of a (nz, ny, nx) uint8 CUDA tensor (vktClahe3DSV); bricks = (bx, by, bz)
     bricks per axis dividing the dims.  Returns the uint8 result tensor."""

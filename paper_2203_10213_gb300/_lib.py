@@ -61,6 +61,7 @@ SIGNATURES = {
     "vktBrickDecomposeCountSV": [pi32, pi32, pi32, p, i32, i32, i32],
     "vktBrickDecomposeSV": [ctypes.POINTER(ctypes.c_void_p), i32, p, i32, i32, i32, i32],
     "vktClahe3DSV": [p, p, i32, i32, i32, ctypes.c_float],
+    "vktRenderSV": [p, i32, i32, p, p],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],

@@ -172,6 +172,38 @@ def test_clahe_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+def test_render_validation_without_device(vkt, lib):
+    import numpy as np
+    v = ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(v), ctypes.c_void_p(0x100000), 8, 8, 8,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 0
+    lut = np.array([[0, 0, 0, 0], [1, 1, 1, 1]], dtype=np.float32)
+
+    def params(**kw):
+        p = vkt.RenderParams()
+        p.eye[:] = kw.get("eye", (4, 4, -10))
+        p.center[:] = (4, 4, 4)
+        p.up[:] = kw.get("up", (0, 1, 0))
+        p.fovy, p.step, p.termination = kw.get("fovy", 0.8), kw.get("step", 0.5), 2.0
+        p.background[:] = (0, 0, 0, 0)
+        p.lutSize = kw.get("n", 2)
+        p.lut = lut.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        return ctypes.cast(ctypes.pointer(p), ctypes.c_void_p), p
+
+    img = ctypes.c_void_p(0x400000)
+    R = lib.vktRenderSV
+    for kw in (dict(up=(0, 0, 1)), dict(step=0.0), dict(fovy=0.0), dict(fovy=3.5), dict(n=1),
+               dict(n=257), dict(eye=(4, 4, 4))):
+        ptr, keep = params(**kw)
+        assert R(img, 8, 8, v, ptr) == 1, kw
+    ptr, keep = params()
+    assert R(img, 0, 8, v, ptr) == 1
+    assert R(ctypes.c_void_p(0x400004), 8, 8, v, ptr) == 1     # image not 16-byte aligned
+    assert R(img, 8, 8, None, ptr) == 2
+    assert R(img, 8, 8, v, ptr) == 6                            # valid: reaches the device check
+    assert lib.vktStructuredVolumeDestroy(v) == 0
+
+
 def test_owning_create_reports_missing_device(vkt, lib):
     import torch
     if torch.cuda.is_available():

@@ -103,7 +103,9 @@ __device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, in
 // so code for unused ways of loading costs instruction cache): 0 = from the arguments
 // (tensor map, row copies or plain loads), 1 = tensor map, 2 = row copies
 constexpr int LM_ANY = 0, LM_TMA = 1, LM_ROWS = 2;
-template <int K, bool ADJ, int SF = -1, int DF = -1, int LM = LM_ANY>
+// ROI: the forward stores are bounded by the arguments' region fields; otherwise by the
+// volume (known at compile time to start at column 0)
+template <int K, bool ADJ, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false>
 __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
@@ -178,8 +180,9 @@ __global__ void __launch_bounds__(NT)
     };
 
     const int ox = x0 + tx * RX;
-    const int nvalid = p.sx1 - ox;
-    const int first = p.sx0 > ox ? p.sx0 - ox : 0;   // leading columns outside the region
+    const int nvalid = (ROI ? p.sx1 : p.nx) - ox;
+    const int first = (ROI && p.sx0 > ox) ? p.sx0 - ox : 0;   // leading columns outside the region
+    const int yend = ROI ? p.sy1 : p.ny;
     bool failed = false;
 
     // One input plane: fetch, convert, multiply into the K output planes, retire one.
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(NT)
                 if (ADJ) {
                     store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
                                           ox, row);
-                } else if (oy < p.sy1 && nvalid > 0) {
+                } else if (oy < yend && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
                     store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
                 }
@@ -407,12 +410,15 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     // tensor-map jobs get kernels without the other ways of loading, and so do row-copy
     // jobs of the compiled-in formats; plain-load jobs take the run-time variant
     auto kern = a.use_tma ? k_direct<K, ADJ, -1, -1, LM_TMA> : k_direct<K, ADJ, -1, -1, LM_ANY>;
+    if constexpr (!ADJ) {
+        if (job.roi) kern = k_direct<K, ADJ, -1, -1, LM_ANY, true>;   // reads the region fields
+    }
     if constexpr (!ADJ && K >= 3 && K <= 5) {
-        if (job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
+        if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
             if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA>;
             else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS>;
         }
-        if (job.dfmt == FMT_F32 && job.sfmt == FMT_F32) {
+        if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_F32) {
             if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA>;
             else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS>;
         }

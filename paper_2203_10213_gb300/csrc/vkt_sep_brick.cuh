@@ -90,7 +90,9 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // TMA so far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring and its
 // barrier phases carry on across bricks.  Returns false if a bounded wait timed out (after recording it and
 // draining the loads in flight).
-template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY>
+// ROI: the job's region fields (origin, store bounds) are read; otherwise the whole volume is
+// assumed at compile time (no region arithmetic in the store path)
+template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
@@ -114,9 +116,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int x0 = J.ox0 + bx * TX, y0 = J.oy0 + by * TY;
-    const int zc0 = J.oz0 + bz * J.zchunk;
-    const int zc1 = min(zc0 + J.zchunk, J.sz1);
+    const int x0 = (ROI ? J.ox0 : 0) + bx * TX, y0 = (ROI ? J.oy0 : 0) + by * TY;
+    const int zc0 = (ROI ? J.oz0 : 0) + bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, ROI ? J.sz1 : J.nz);
     if (zc0 >= zc1) return true;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
@@ -168,8 +170,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             }
 
     const int ox = x0 + tx * RX;
-    const int nvalid = J.sx1 - ox;
-    const int first = J.sx0 > ox ? J.sx0 - ox : 0;   // leading columns outside the region
+    const int nvalid = (ROI ? J.sx1 : J.nx) - ox;
+    const int first = (ROI && J.sx0 > ox) ? J.sx0 - ox : 0;   // leading columns outside the region
+    const int yend = ROI ? J.sy1 : J.ny;
     bool failed = false;
 
     auto plane = [&](const int it, const int u) {
@@ -238,7 +241,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         // stores the completed output plane it - R (once it >= 2R)
         auto store_plane = [&](const float (&rowv)[RX], int i) {
             const int oy = y0 + ty * RY + i;
-            if (it >= 2 * R && oy < J.sy1 && nvalid > 0) {
+            if (it >= 2 * R && oy < yend && nvalid > 0) {
                 const int64_t idx = (static_cast<int64_t>(pfirst + it - R) * J.ny + oy) * J.nx + ox;
                 store_row<RX>(J.dst, dfmt, idx, nvalid, rowv, J.a0, J.a1, J.qmax, first);
             }
@@ -406,7 +409,7 @@ __host__ __device__ constexpr size_t smem_bytes_comp(int sfmt, bool rows = false
            static_cast<size_t>(Geo::FH) * TX * sizeof(float2);           // (hi, lo) x pass
 }
 
-template <int K, class Wt, int LM = LM_ANY>
+template <int K, class Wt, int LM = LM_ANY, bool ROI = false>
 __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUtensorMap* tmap,
                                            int bx, int by, int bz, unsigned char* smem,
                                            uint32_t& gplane, unsigned* status)
@@ -427,9 +430,9 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
-    const int x0 = J.ox0 + bx * TX, y0 = J.oy0 + by * CTY;
-    const int zc0 = J.oz0 + bz * J.zchunk;
-    const int zc1 = min(zc0 + J.zchunk, J.sz1);
+    const int x0 = (ROI ? J.ox0 : 0) + bx * TX, y0 = (ROI ? J.oy0 : 0) + by * CTY;
+    const int zc0 = (ROI ? J.oz0 : 0) + bz * J.zchunk;
+    const int zc1 = min(zc0 + J.zchunk, ROI ? J.sz1 : J.nz);
     if (zc0 >= zc1) return true;
     const int pfirst = zc0 - R;
     const int nplanes = zc1 - zc0 + 2 * R;
@@ -467,8 +470,9 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
 
     const int ox = x0 + tx * RX;
     const int oy = y0 + ty;
-    const int nvalid = J.sx1 - ox;
-    const int first = J.sx0 > ox ? J.sx0 - ox : 0;   // leading columns outside the region
+    const int nvalid = (ROI ? J.sx1 : J.nx) - ox;
+    const int first = (ROI && J.sx0 > ox) ? J.sx0 - ox : 0;   // leading columns outside the region
+    const int yend = ROI ? J.sy1 : J.ny;
     bool failed = false;
 
     auto plane = [&](const int it, const int u) {
@@ -549,7 +553,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             for (int x = 0; x < RX; ++x) dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
         }
         const int sl0 = ((u - R) % K + K) % K;
-        if (it >= 2 * R && oy < J.sy1 && nvalid > 0) {
+        if (it >= 2 * R && oy < yend && nvalid > 0) {
             const int oz = pfirst + it - R;
             const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
 #pragma unroll

@@ -17,7 +17,7 @@ constexpr int sep_min_blocks() { return K <= 5 ? 3 : 2; }
 
 // SF/DF: source and destination formats fixed at compile time (-1: read from the job);
 // LM: the way stages are filled (sep::LM_*), fixed at compile time where known
-template <int K, int SF = -1, int DF = -1, int LM = sep::LM_ANY>
+template <int K, int SF = -1, int DF = -1, int LM = sep::LM_ANY, bool ROI = false>
 __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     k_separable(const __grid_constant__ CUtensorMap tmap, const sep::Job J, const sep::W<K> G,
                 unsigned* status)
@@ -29,11 +29,11 @@ __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick<K, sep::W<K>, SF, DF, LM>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
-                                         gplane, status);
+    sep::brick<K, sep::W<K>, SF, DF, LM, ROI>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
+                                              smem, gplane, status);
 }
 
-template <int K, int LM = sep::LM_ANY>
+template <int K, int LM = sep::LM_ANY, bool ROI = false>
 __global__ void __launch_bounds__(sep::NT)
     k_separable_comp(const __grid_constant__ CUtensorMap tmap, const sep::Job J,
                      const sep::W<K> G, unsigned* status)
@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(sep::NT)
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick_comp<K, sep::W<K>, LM>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
-                                      gplane, status);
+    sep::brick_comp<K, sep::W<K>, LM, ROI>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
+                                           gplane, status);
 }
 
 // the kernel for a job: tensor-map jobs and (for the compiled-in formats) row-copy jobs get
@@ -133,6 +133,11 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         if (!J.comp && J.dfmt == FMT_F32 && J.sfmt == FMT_F32) fast = pick_fast<K, FMT_F32, FMT_F32>(J);
     }
     auto comp = J.use_tma ? k_separable_comp<K, sep::LM_TMA> : k_separable_comp<K, sep::LM_ANY>;
+    if (job.roi) {
+        // region calls take the run-time variants that read the region fields
+        fast = k_separable<K, -1, -1, sep::LM_ANY, true>;
+        comp = k_separable_comp<K, sep::LM_ANY, true>;
+    }
     cudaError_t e = J.comp ? cudaFuncSetAttribute(comp,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem))

@@ -69,6 +69,25 @@ struct W {
     float gx[K], gy[K], gz[K];
 };
 
+// FX: the x pass reads the raw tensor-map stage directly (converting as it loads) into one of
+// two x-pass tiles, so a plane needs one CTA barrier instead of two and no float tile.  For
+// float32 sources with tensor-map loads (17-21 % faster at k = 3, 5), and uint8 at k = 3 only
+// (9 % faster; at k = 5 and 7 the k + 3 byte loads per x-pass item cost more than the
+// barrier saves: 3 % and 20 % slower)
+template <int LM, int SF, int K>
+__host__ __device__ constexpr bool fused_x()
+{
+    return LM == LM_TMA && (SF == FMT_F32 || (SF == FMT_U8 && K == 3));
+}
+
+template <int K>
+__host__ __device__ constexpr size_t smem_bytes_fx(int sfmt)
+{
+    using Geo = Brick<K, TX, TY>;
+    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, false) +
+           2 * static_cast<size_t>(Geo::FH) * TX * sizeof(float);
+}
+
 template <int K>
 __host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 {
@@ -111,8 +130,9 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const int rawb = Geo::stage_bytes(sfmt, rows);
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
+    constexpr bool FX = fused_x<LM, SF, K>();
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
-    float* T1 = F + FH * FP;
+    float* T1 = FX ? F : F + FH * FP;     // FX: two x-pass tiles, no float tile
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
@@ -180,6 +200,70 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
+        if constexpr (FX) {
+            float* T1b = T1 + (it & 1) * FH * TX;
+            ok = mbar_wait(&bars[s], (q / STAGES) & 1);
+            // x pass straight from the raw stage: T1b[row][x] = sum_a gx[a] v(x + a - r), the
+            // source voxels converted as they are loaded, clamped in x only at the volume's
+            // x faces (the rows are clamped through the stage row read)
+            constexpr int RWE = TX + 2 * fmt_xalign(SF);   // raw row length in voxels
+            const bool xin = x0 - R >= 0 && x0 + TX - 1 + R <= J.nx - 1;
+            if (ok) {
+#pragma unroll
+                for (int n = 0; n < (XITEMS + NT - 1) / NT; ++n) {
+                    const int item = tid + n * NT;
+                    if (item < XITEMS) {
+                        const int row = item / XGROUPS, g = item - row * XGROUPS;
+                        const int rrow = clampi(y0 - R + row, 0, J.ny - 1) - (y0 - R);
+                        float win[4 + K - 1];
+                        if constexpr (SF == FMT_U8) {
+                            const unsigned char* rp = rs + rrow * RWE;
+                            if (xin) {
+#pragma unroll
+                                for (int e = 0; e < 4 + K - 1; ++e)
+                                    win[e] = static_cast<float>(rp[4 * g - R + xa + e]);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4 + K - 1; ++e)
+                                    win[e] = static_cast<float>(
+                                        rp[clampi(x0 + 4 * g - R + e, 0, J.nx - 1) - (x0 - xa)]);
+                            }
+                        } else {
+                            const float* rp = reinterpret_cast<const float*>(rs) + rrow * RWE;
+                            if (xin) {
+#pragma unroll
+                                for (int e = 0; e < 4 + K - 1; ++e) win[e] = rp[4 * g - R + xa + e];
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4 + K - 1; ++e)
+                                    win[e] = rp[clampi(x0 + 4 * g - R + e, 0, J.nx - 1) - (x0 - xa)];
+                            }
+                        }
+                        float4 o;
+                        float* op = &o.x;
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            float t = 0.f;
+#pragma unroll
+                            for (int a = 0; a < K; ++a) t = fmaf(G.gx[a], win[x + a], t);
+                            op[x] = t;
+                        }
+                        *reinterpret_cast<float4*>(T1b + row * TX + 4 * g) = o;
+                    }
+                }
+            }
+            // the stage is read and the x-pass tile written by every thread
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                return;
+            }
+            if (tid == 0 && it + STAGES < nplanes) {
+                mbar_arrive_expect_tx(&bars[s], txb);
+                tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
+                            clampi(pfirst + it + STAGES, 0, J.nz - 1));
+                ++issued;
+            }
+        } else {
         if (tma || rows) {
             ok = mbar_wait(&bars[s], (q / STAGES) & 1);
         } else {
@@ -236,6 +320,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             mbar_arrive(&bars[s]);
             ++issued;
         }
+        }   // not FX
+        const float* T1y = FX ? T1 + (it & 1) * FH * TX : T1;
         // y pass into registers, then the z pass into the K rotating accumulator planes
         const int sl0 = ((u - R) % K + K) % K;
         // stores the completed output plane it - R (once it >= 2R)
@@ -251,7 +337,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 #pragma unroll
             for (int j = 0; j < RY + K - 1; ++j) {
                 float v[RX];
-                load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
+                load_row<RX, RX>(T1y + (ty * RY + j) * TX + tx * RX, v);
 #pragma unroll
                 for (int i = 0; i < RY; ++i) {
                     const int b = j - i;
@@ -296,7 +382,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 #pragma unroll
             for (int j = 0; j < RY + K - 1; ++j) {
                 float v[RX];
-                load_row<RX, RX>(T1 + (ty * RY + j) * TX + tx * RX, v);
+                load_row<RX, RX>(T1y + (ty * RY + j) * TX + tx * RX, v);
 #pragma unroll
                 for (int i = 0; i < RY; ++i) {
                     const int b = j - i;

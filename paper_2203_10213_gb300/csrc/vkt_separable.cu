@@ -124,8 +124,8 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     // per row, when the volume starts on a 16-byte boundary
     J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
     if (!J.use_tma) memset(&map, 0, sizeof(map));
-    const size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt, J.rows != 0)
-                               : sep::smem_bytes<K>(job.sfmt, J.rows != 0);
+    size_t smem = J.comp ? sep::smem_bytes_comp<K>(job.sfmt, J.rows != 0)
+                         : sep::smem_bytes<K>(job.sfmt, J.rows != 0);
     // the common float32 destinations get kernels with their formats compiled in
     auto fast = pick_fast<K, -1, -1>(J);
     if constexpr (K >= 3 && K <= 7) {
@@ -138,6 +138,11 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         fast = k_separable<K, -1, -1, sep::LM_ANY, true>;
         comp = k_separable_comp<K, sep::LM_ANY, true>;
     }
+    // the tensor-map kernels of the compiled-in formats fuse the conversion into the x pass
+    // (their own shared-memory layout)
+    if (!job.roi && !J.comp && J.use_tma && J.dfmt == FMT_F32 &&
+        (J.sfmt == FMT_F32 || (J.sfmt == FMT_U8 && K == 3)) && K >= 3 && K <= 7)
+        smem = std::max(smem, sep::smem_bytes_fx<K>(job.sfmt));
     cudaError_t e = J.comp ? cudaFuncSetAttribute(comp,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem))

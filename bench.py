@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--precision-reps", type=int, default=10)
     ap.add_argument("--no-batching-form", action="store_true",
                     help="skip the 256-volume graph batch vs separate launches comparison")
+    ap.add_argument("--no-extra-forms", action="store_true",
+                    help="skip the range, BrickDecompose, CLAHE-3D and render forms")
     ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES),
                     help="run one kernel configuration --reps times and exit (for ncu captures)")
     ap.add_argument("--reps", type=int, default=3)
@@ -659,12 +661,14 @@ def run_ours(args):
     bform = None
     if not args.no_batching_form:
         bform = batching_form(args, vkt, torch, dev, stream)
-    kform = brick_form(vkt, torch, stream, src)
-    cform = clahe_form(vkt, torch, stream)
-    vform = render_form(vkt, torch, stream, src)
-    g_roi = vkt.Filter.gaussian(5, 1.5)
-    rform = range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g_roi, lap)
-    g_roi.destroy()
+    kform = cform = vform = rform = None
+    if not args.no_extra_forms:
+        kform = brick_form(vkt, torch, stream, src)
+        cform = clahe_form(vkt, torch, stream)
+        vform = render_form(vkt, torch, stream, src)
+        g_roi = vkt.Filter.gaussian(5, 1.5)
+        rform = range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g_roi, lap)
+        g_roi.destroy()
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),

@@ -73,6 +73,9 @@ def _load():
             lib.oracle_render.restype = i32
             lib.oracle_render.argtypes = [p, i32, d, d, i64, i64, i64, i32, i32, p, p, p, d, d, d,
                                           p, i32, p, p]
+            lib.oracle_render_pixels.restype = i32
+            lib.oracle_render_pixels.argtypes = [p, i32, d, d, i64, i64, i64, i32, i32, p, p, p, d, d,
+                                                 d, p, i32, p, p, i64, p]
             lib.oracle_clahe3d.restype = i32
             lib.oracle_clahe3d.argtypes = [p, i64, i64, i64, i32, i32, i32, d, p, p, p]
             _lib = lib
@@ -272,4 +275,25 @@ def render(src: np.ndarray, lo: float, hi: float, width: int, height: int, eye, 
                                float(termination), _ptr(bg), lut.shape[0], _ptr(lut), _ptr(out))
     if rc != 0:
         raise ValueError("oracle_render: bad arguments")
+    return out
+
+
+def render_pixels(src: np.ndarray, lo: float, hi: float, width: int, height: int, eye, center,
+                  up, fovy: float, step: float, termination: float, background, lut, pixels):
+    """``render`` for the listed pixels only: pixels is an (n, 2) array of (px, py); returns
+    (n, 4) float64 RGBA."""
+    src = np.ascontiguousarray(src)
+    fmt = _fmt_of(src)
+    nz, ny, nx = src.shape
+    lut = _c(lut, np.float64).reshape(-1, 4)
+    pix = _c(pixels, np.int32).reshape(-1, 2)
+    out = np.empty((pix.shape[0], 4), dtype=np.float64)
+    vec = lambda v: _c(v, np.float64).reshape(-1)
+    e, c, u, bg = vec(eye), vec(center), vec(up), vec(background)
+    rc = _load().oracle_render_pixels(_ptr(src), fmt, float(lo), float(hi), nx, ny, nz, int(width),
+                                      int(height), _ptr(e), _ptr(c), _ptr(u), float(fovy),
+                                      float(step), float(termination), _ptr(bg), lut.shape[0],
+                                      _ptr(lut), _ptr(pix), pix.shape[0], _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_render_pixels: bad arguments")
     return out

@@ -443,10 +443,28 @@ static void normalize3(double* v)
     v[2] /= n;
 }
 
+/* the pixels listed in pix (npix (px, py) pairs; all pixels when pix is NULL) */
+int oracle_render_pixels(const void* src, int fmt, double lo, double hi, int64_t nx, int64_t ny,
+                         int64_t nz, int width, int height, const double* eye,
+                         const double* center, const double* up, double fovy, double step,
+                         double termination, const double* bg, int lut_n, const double* lut,
+                         const int32_t* pix, int64_t npix, double* rgba);
+
 int oracle_render(const void* src, int fmt, double lo, double hi, int64_t nx, int64_t ny,
                   int64_t nz, int width, int height, const double* eye, const double* center,
                   const double* up, double fovy, double step, double termination,
                   const double* bg, int lut_n, const double* lut, double* rgba)
+{
+    return oracle_render_pixels(src, fmt, lo, hi, nx, ny, nz, width, height, eye, center, up,
+                                fovy, step, termination, bg, lut_n, lut, NULL,
+                                (int64_t)width * height, rgba);
+}
+
+int oracle_render_pixels(const void* src, int fmt, double lo, double hi, int64_t nx, int64_t ny,
+                         int64_t nz, int width, int height, const double* eye,
+                         const double* center, const double* up, double fovy, double step,
+                         double termination, const double* bg, int lut_n, const double* lut,
+                         const int32_t* pix, int64_t npix, double* rgba)
 {
     if (width < 1 || height < 1 || lut_n < 2 || !(step > 0.0)) return -1;
     double f[3] = {center[0] - eye[0], center[1] - eye[1], center[2] - eye[2]};
@@ -456,9 +474,10 @@ int oracle_render(const void* src, int fmt, double lo, double hi, int64_t nx, in
     const double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
     const double th = tan(0.5 * fovy), aspect = (double)width / (double)height;
     const double box[3] = {(double)nx, (double)ny, (double)nz};
-#pragma omp parallel for schedule(dynamic, 4)
-    for (int py = 0; py < height; ++py)
-        for (int px = 0; px < width; ++px) {
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t n = 0; n < npix; ++n) {
+            const int px = pix ? pix[2 * n] : (int)(n % width);
+            const int py = pix ? pix[2 * n + 1] : (int)(n / width);
             const double sx = (2.0 * (px + 0.5) / width - 1.0) * th * aspect;
             const double sy = (1.0 - 2.0 * (py + 0.5) / height) * th;
             double d[3] = {f[0] + sx * r[0] + sy * u[0], f[1] + sx * r[1] + sy * u[1],
@@ -503,7 +522,7 @@ int oracle_render(const void* src, int fmt, double lo, double hi, int64_t nx, in
                     if (A >= termination) break;
                 }
             }
-            double* o = rgba + 4 * ((int64_t)py * width + px);
+            double* o = rgba + 4 * (pix ? n : ((int64_t)py * width + px));
             for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + (1.0 - A) * bg[ch];
             o[3] = A + (1.0 - A) * bg[3];
         }

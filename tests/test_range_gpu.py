@@ -127,3 +127,33 @@ def test_empty_box_writes_nothing_and_tensor_path_is_refused():
     with pytest.raises(vkt.VktError) as e:
         vkt.filter_tensor(src, filt, out=out, path="tensor", roi=((0, 0, 0), (8, 8, 8)))
     assert e.value.code == 4     # VKT_ERROR_UNSUPPORTED
+
+
+def test_range_full_size_sampled():
+    """The bench's region, 300 x 250 x 270 voxels off every boundary of the 512^3 uint8
+    CT-like volume, both filters of the benchmark step: seeded voxels inside the box
+    against the oracle's per-voxel evaluation, voxels outside unchanged."""
+    src = synth.volume("blobs", synth.U8, (512, 512, 512), synth.BASE_SEED + 1)
+    (x0, y0, z0), (x1, y1, z1) = (101, 77, 130), (401, 327, 400)
+    s = torch.from_numpy(src).cuda()
+    rng = np.random.default_rng(SEED + 77)
+    n = 4000
+    idx = np.stack([rng.integers(z0, z1, n), rng.integers(y0, y1, n), rng.integers(x0, x1, n)], axis=1)
+    # the box's corners and faces
+    corners = np.array([[z, y, x] for z in (z0, z1 - 1) for y in (y0, y1 - 1) for x in (x0, x1 - 1)])
+    idx = np.concatenate([corners, idx])
+    outside = np.stack([rng.integers(0, 512, n), rng.integers(0, 512, n), rng.integers(0, 512, n)], axis=1)
+    keep = ~((outside[:, 0] >= z0) & (outside[:, 0] < z1) & (outside[:, 1] >= y0) & (outside[:, 1] < y1)
+             & (outside[:, 2] >= x0) & (outside[:, 2] < x1))
+    outside = outside[keep]
+    for filt, w in ((vkt.Filter.gaussian(5, 1.5), oracle.gaussian_weights(5, float(np.float32(1.5)))),
+                    (vkt.Filter.dense(oracle.laplacian_3().astype(np.float32)), oracle.laplacian_3())):
+        out = torch.full(src.shape, -3.0, dtype=torch.float32, device="cuda")
+        vkt.filter_tensor(s, filt, out=out, roi=((x0, y0, z0), (x1, y1, z1)))
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        lin = (idx[:, 0] * 512 + idx[:, 1]) * 512 + idx[:, 2]      # linear voxel numbers
+        ref = oracle.correlate_points(src, w, lin, 0.0, 1.0)
+        err = np.max(np.abs(got[idx[:, 0], idx[:, 1], idx[:, 2]] - ref)) / oracle.error_scale(w, 1.0)
+        assert err <= 1e-5, err
+        assert np.all(got[outside[:, 0], outside[:, 1], outside[:, 2]] == -3.0)

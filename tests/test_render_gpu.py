@@ -84,3 +84,23 @@ def test_render_rejects_bad_parameters():
         vkt.render(v, 8, 8, (4, 4, -10), (4, 4, 4), (0, 1, 0), 0.8, 0.0, RAMP)   # zero step
     with pytest.raises(vkt.VktError):
         vkt.render(v, 8, 8, (4, 4, -10), (4, 4, 4), (0, 1, 0), 0.8, 0.5, RAMP[:1])  # one entry
+
+
+def test_render_full_size_sampled():
+    """The bench's frame: 1024 x 768 of the 512^3 uint8 CT-like volume, step 0.5, the ramp
+    table; 2000 seeded pixels (and the four corners and the centre) against the oracle."""
+    v = synth.volume("blobs", synth.U8, (512, 512, 512), synth.BASE_SEED + 1)
+    W, H = 1024, 768
+    eye, center, up, fovy = (256.0, 300.0, -600.0), (256.0, 256.0, 256.0), (0.0, 1.0, 0.0), 0.8
+    lut = np.array([[0, 0, 0, 0], [0.9, 0.5, 0.2, 0.02], [1, 0.9, 0.6, 0.15], [1, 1, 1, 0.6]], np.float32)
+    img = vkt.render(torch.from_numpy(v).cuda(), W, H, eye, center, up, fovy, 0.5, lut)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(SEED + 55)
+    pix = np.concatenate([np.array([[0, 0], [W - 1, 0], [0, H - 1], [W - 1, H - 1], [W // 2, H // 2]]),
+                          np.stack([rng.integers(0, W, 2000), rng.integers(0, H, 2000)], axis=1)])
+    f32 = lambda x: [float(np.float32(t)) for t in x]
+    ref = oracle.render_pixels(v, 0.0, 1.0, W, H, f32(eye), f32(center), f32(up),
+                               float(np.float32(fovy)), 0.5, 2.0, (0, 0, 0, 0), lut, pix)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]].astype(np.float64)
+    err = np.max(np.abs(got - ref))
+    assert err <= TOL, f"max |gpu - oracle| = {err:.2e}"

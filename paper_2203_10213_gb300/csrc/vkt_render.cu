@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(BX* BY) k_render(const __grid_constant__ Rende
             const float cg = e0[1] * (1.f - w) + e0[5] * w;
             const float cb = e0[2] * (1.f - w) + e0[6] * w;
             const float ca = e0[3] * (1.f - w) + e0[7] * w;
-            const float ac = 1.f - powf(1.f - ca, a.step);
+            // opacity corrected to the step: 1 - (1 - a)^step = 1 - 2^(step log2(1 - a))
+            const float ac = 1.f - exp2f(a.step * __log2f(1.f - ca));
             const float tw = (1.f - A) * ac;
             C0 += tw * cr;
             C1 += tw * cg;

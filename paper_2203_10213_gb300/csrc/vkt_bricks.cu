@@ -6,8 +6,10 @@
 // voxel (i, j, k) is the source voxel clamp(o - g + (i, j, k)): ghost cells inside the volume
 // copy the neighbouring bricks' voxels, ghost cells beyond a face repeat the face voxel (the
 // clamp-to-edge rule of ApplyFilter).  One launch copies every brick: a CTA takes a run of
-// brick rows, a warp four rows at a time, the lanes consecutive x (coalesced reads and
-// writes).
+// brick rows.  With a 16-byte aligned source and 4-byte aligned bricks (every torch
+// allocation) the rows are staged in shared memory by asynchronous 16-byte copies and
+// written as blocks or words (k_bricks_staged); otherwise a warp copies four rows at a
+// time, its lanes consecutive x (k_bricks).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +21,7 @@ namespace vkt {
 namespace {
 
 constexpr int NT = 256;
+constexpr int NWARP = NT / 32;
 constexpr int MIN_ROWS_PER_CTA = 64;
 
 struct BrickDesc {
@@ -90,6 +93,225 @@ __global__ void __launch_bounds__(NT)
                     if (c0 + 32 * e < n) d[q][c0 + 32 * e] = v[q][e];
             }
         }
+    }
+}
+
+// Staged variant (16-byte aligned source, 4-byte aligned bricks).  Byte-wide loads keep too
+// few bytes in flight for short brick rows, so a CTA stages a batch of brick rows in shared
+// memory first: for every row, the 16-byte blocks that cover its clamp-free source span,
+// fetched with asynchronous 16-byte copies (no registers held while in flight; two buffers,
+// so one batch's copies fly while the previous batch is written).  Then the CTA writes the
+// batch's destination bytes, which are contiguous in the brick: as 16-byte blocks when
+// rows and spans are 16-byte aligned and unclamped; as words on fixed (row, word) lane
+// slots when rows are whole words and the slots keep most lanes busy; else as one run of
+// words over the batch.  A word inside a row's span is one funnel shift of two staged
+// words; words that touch the clamped columns or straddle two rows are assembled byte by
+// byte.  Every brick byte maps to a staged byte: the clamped columns repeat the span's
+// first or last voxel.
+constexpr int ST_BUDGET = 24 * 1024;   // staged bytes per CTA (both buffers)
+constexpr int ST_MAXROWS = 256;        // rows per batch (a multiple of 4)
+
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void* gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_group1()
+{
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// ES: bytes per voxel.  rows_per_cta and rb (rows per staged batch) are multiples of 4, so a
+// batch's first destination byte is 4-byte aligned; pitch: staged bytes per row (a multiple
+// of 16, at least 16 more than the widest span's covering blocks need).  Shared memory: two
+// buffers of rb x pitch bytes.
+// Off: the type of source byte offsets (uint32_t for volumes below 2^31 bytes).
+template <int ES, typename Off>
+__global__ void __launch_bounds__(NT)
+    k_bricks_staged(const unsigned char* __restrict__ src, int nx, int ny, int nz,
+                    uint64_t vol_bytes, const BrickDesc* __restrict__ bricks, int ghost,
+                    int rows_per_cta, int rb, int pitch)
+{
+    extern __shared__ __align__(16) unsigned char st[];
+    __shared__ int s_shift[2][ST_MAXROWS];
+    const BrickDesc b = bricks[blockIdx.y];
+    const int rows = b.dy * b.dz;
+    const int r0 = blockIdx.x * rows_per_cta;
+    if (r0 >= rows) return;
+    const int r1 = min(rows, r0 + rows_per_cta);
+    const int tid = threadIdx.x;
+    const int sx0 = b.ox - ghost;
+    const int left = clampd(-sx0, 0, b.dx);
+    const int right = clampd(nx - sx0, left, b.dx);
+    const int nb = (right - left) * ES;                 // span bytes (at least one voxel)
+    const int lb = left * ES, rbyte = right * ES;       // span within the brick row, bytes
+    const int L = b.dx * ES;                            // brick row bytes
+    const int nv = (nb + 30) / 16;                      // covering blocks, any alignment
+    const Off sb = static_cast<Off>(sx0 + left) * ES;
+    unsigned char* dst = static_cast<unsigned char*>(b.dst);
+    // the thread's words advance by 4 NT bytes: DR rows and DC bytes
+    const int DR = (4 * NT) / L, DC = (4 * NT) - DR * L;
+
+    // stage the spans of rows q0 .. q0 + nr - 1 into buffer buf (one async-copy group)
+    // lanes of a warp take (row, block) slots: rpw rows of nv blocks per warp pass when the
+    // blocks fit in a warp, else one row with the lanes striding over its blocks
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rpw = nv <= 32 ? 32 / nv : 1;
+    const int lrow = nv <= 32 ? lane / nv : 0;
+    const int lv0 = nv <= 32 ? lane - lrow * nv : lane;
+    const int rstep = NWARP * rpw;
+    // the same slots for writing: 16-byte blocks (v16) or words of a row
+    const bool v16 = lb == 0 && rbyte == L && (L & 15) == 0 && ((nx * ES) & 15) == 0 && (sb & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    const int vpr16 = L >> 4, wpr4 = L >> 2;
+    const int rpw16 = vpr16 >= 1 && vpr16 <= 32 ? 32 / vpr16 : 1;
+    const int lrow16 = vpr16 >= 1 && vpr16 <= 32 ? lane / vpr16 : 0;
+    const int lv16 = vpr16 >= 1 && vpr16 <= 32 ? lane - lrow16 * vpr16 : lane;
+    const int rpw4 = wpr4 >= 1 && wpr4 <= 32 ? 32 / wpr4 : 1;
+    const int lrow4 = wpr4 >= 1 && wpr4 <= 32 ? lane / wpr4 : 0;
+    const int lw4 = wpr4 >= 1 && wpr4 <= 32 ? lane - lrow4 * wpr4 : lane;
+    const bool words = (L & 3) == 0 && (wpr4 <= 32 ? 4 * rpw4 * wpr4 >= 3 * 32
+                                                   : 4 * wpr4 >= 3 * 32 * ((wpr4 + 31) / 32));
+    auto stage = [&](int q0, int nr, int buf) {
+        const int boff = buf * rb * pitch;
+        const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(st)) + boff;
+        int* sh = s_shift[buf];
+        int rr = warp * rpw + lrow;
+        if (lrow >= rpw || rr >= nr) {
+            cp_async_commit();
+            return;
+        }
+        int k = (q0 + rr) / b.dy, j = q0 + rr - k * b.dy;
+        for (; rr < nr; rr += rstep) {
+            const int sz = clampd(b.oz - ghost + k, 0, nz - 1);
+            const int sy = clampd(b.oy - ghost + j, 0, ny - 1);
+            const Off a = (static_cast<Off>(sz) * ny + sy) * nx * ES + sb;
+            const Off a16 = a & ~Off(15);
+            if (lv0 == 0) sh[rr] = static_cast<int>(a - a16);
+            for (int v = lv0; v < nv; v += 32) {
+                const Off g = a16 + 16u * v;
+                if (g >= a + nb) break;                 // past the span (smaller shift)
+                const int so = rr * pitch + 16 * v;
+                if (static_cast<uint64_t>(g) + 16 <= vol_bytes) {
+                    cp_async16(sbase + so, src + g);
+                } else {
+                    for (int e = 0; e < 16; ++e)
+                        if (static_cast<uint64_t>(g) + e < vol_bytes) st[boff + so + e] = src[g + e];
+                }
+            }
+            j += rstep;
+            while (j >= b.dy) {
+                j -= b.dy;
+                ++k;
+            }
+        }
+        cp_async_commit();
+    };
+
+    // two buffers: the next batch's copies are in flight while this batch is written
+    stage(r0, min(rb, r1 - r0), 0);
+    for (int q0 = r0, buf = 0; q0 < r1; q0 += rb, buf ^= 1) {
+        const int nr = min(rb, r1 - q0);
+        if (q0 + rb < r1) {
+            stage(q0 + rb, min(rb, r1 - q0 - rb), buf ^ 1);
+            cp_async_wait_group1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const int boff = buf * rb * pitch;                 // buffer start in st (16-aligned)
+        const uint32_t* sw = reinterpret_cast<const uint32_t*>(st + boff);
+        const int* s_sh = s_shift[buf];
+        // brick bytes [q0 L, (q0 + nr) L); byte c of batch row rr comes from staged byte
+        // pos(c) of that row
+        unsigned char* d0 = dst + static_cast<int64_t>(q0) * L;
+        if (v16) {
+            // whole rows, every span 16-byte aligned: 16-byte copies, lanes on (row, block)
+            // slots as in the staging
+            const uint4* s4 = reinterpret_cast<const uint4*>(st + boff);
+            uint4* d4 = reinterpret_cast<uint4*>(d0);
+            const int vpr = L >> 4;
+            for (int r = warp * rpw16 + lrow16; lrow16 < rpw16 && r < nr; r += NWARP * rpw16)
+                for (int v = lv16; v < vpr; v += 32) d4[r * vpr + v] = s4[(r * pitch >> 4) + v];
+        } else if (words) {
+            // rows of whole words, slots keeping at least 3/4 of the lanes busy: lanes on
+            // (row, word) slots
+            const int wpr = L >> 2;
+            uint32_t* dw = reinterpret_cast<uint32_t*>(d0);
+            for (int r = warp * rpw4 + lrow4; lrow4 < rpw4 && r < nr; r += NWARP * rpw4) {
+                const int sh = s_sh[r];
+                for (int w = lw4; w < wpr; w += 32) {
+                    const int col = 4 * w;
+                    uint32_t v;
+                    if (col >= lb && col + 4 <= rbyte) {
+                        const int bo = r * pitch + sh + (col - lb);
+                        v = __funnelshift_r(sw[bo >> 2], sw[(bo >> 2) + 1], 8u * static_cast<uint32_t>(bo & 3));
+                    } else {
+                        v = 0;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = col + e;
+                            const int pos = c < lb ? c % ES : (c >= rbyte ? nb - ES + (c - rbyte) % ES : c - lb);
+                            v |= uint32_t(st[boff + r * pitch + sh + pos]) << (8 * e);
+                        }
+                    }
+                    __stwb(dw + r * wpr + w, v);
+                }
+            }
+        } else {
+        // rows of any length: the batch's bytes as one run of words (a word may straddle
+        // two rows)
+        const int nbytes = nr * L;
+        uint32_t* dw = reinterpret_cast<uint32_t*>(d0);
+        int rr = (4 * tid) / L, col = 4 * tid - rr * L;
+        for (int w = tid; 4 * w < nbytes; w += NT) {
+            uint32_t v;
+            if (col >= lb && col + 4 <= rbyte) {
+                const int bo = rr * pitch + s_sh[rr] + (col - lb);
+                v = __funnelshift_r(sw[bo >> 2], sw[(bo >> 2) + 1], 8u * static_cast<uint32_t>(bo & 3));
+            } else {
+                int r = rr, c = col;
+                v = 0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (c >= L) {
+                        c -= L;
+                        ++r;
+                    }
+                    if (4 * w + e < nbytes) {
+                        const int pos = c < lb ? c % ES : (c >= rbyte ? nb - ES + (c - rbyte) % ES : c - lb);
+                        v |= uint32_t(st[boff + r * pitch + s_sh[r] + pos]) << (8 * e);
+                    }
+                    ++c;
+                }
+            }
+            if (4 * w + 4 <= nbytes) {
+                __stwb(dw + w, v);
+            } else {
+                unsigned char* d8 = reinterpret_cast<unsigned char*>(dw + w);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * w + e < nbytes) d8[e] = static_cast<unsigned char>(v >> (8 * e));
+            }
+            col += DC;
+            rr += DR;
+            if (col >= L) {
+                col -= L;
+                ++rr;
+            }
+        }
+        }
+        __syncthreads();   // buffer buf is refilled by the batch after next
     }
 }
 
@@ -176,32 +398,67 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     }
     const int64_t total_rows = static_cast<int64_t>(max_rows) * numBricks;
     const int64_t want = std::max<int64_t>(MIN_ROWS_PER_CTA, total_rows / (static_cast<int64_t>(sms) * 32));
-    const int rows_per_cta = static_cast<int>(std::min<int64_t>(want, max_rows));
+    int rows_per_cta = static_cast<int>(std::min<int64_t>(want, max_rows));
+    // staged kernel: 16-byte aligned source, 4-byte aligned bricks, spans short enough that
+    // a batch holds at least 4 rows
+    bool staged = (reinterpret_cast<uintptr_t>(volume->data) & 15) == 0;
+    int pitch = 0;
+    for (const BrickDesc& d : desc) {
+        staged = staged && (reinterpret_cast<uintptr_t>(d.dst) & 3) == 0;
+        const int sx0 = d.ox - ghost;
+        const int left = std::min(std::max(-sx0, 0), d.dx);
+        const int right = std::min(std::max(nx - sx0, left), d.dx);
+        const int nb = (right - left) * es;
+        pitch = std::max(pitch, (nb + 30) / 16 * 16 + 16);
+    }
+    int rb = std::min(ST_MAXROWS, (ST_BUDGET / (2 * std::max(pitch, 1))) & ~3);
+    staged = staged && rb >= 4;
+    if (staged) {
+        rows_per_cta = (rows_per_cta + 3) & ~3;
+        rb = std::min(rb, rows_per_cta);
+    }
     const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
     int launches = 0;
     // at most 65535 bricks per launch (grid y)
     for (int first = 0; e == cudaSuccess && first < numBricks; first += 65535) {
         const int nb = std::min(65535, numBricks - first);
         const dim3 grid(gx, nb);
-        if (es == 1)
+        const unsigned char* s8 = static_cast<const unsigned char*>(volume->data);
+        if (staged) {
+            const size_t sm = 2 * static_cast<size_t>(rb) * pitch;
+            const bool small = sbytes < (uint64_t(1) << 31);
+#define VKT_BRICKS_STAGED(E, O)                                                                      \
+    k_bricks_staged<E, O><<<grid, NT, sm, ctx.stream>>>(s8, nx, ny, nz, sbytes, dtab + first, ghost, \
+                                                        rows_per_cta, rb, pitch)
+            if (es == 1) {
+                if (small) VKT_BRICKS_STAGED(1, uint32_t); else VKT_BRICKS_STAGED(1, uint64_t);
+            } else if (es == 2) {
+                if (small) VKT_BRICKS_STAGED(2, uint32_t); else VKT_BRICKS_STAGED(2, uint64_t);
+            } else {
+                if (small) VKT_BRICKS_STAGED(4, uint32_t); else VKT_BRICKS_STAGED(4, uint64_t);
+            }
+#undef VKT_BRICKS_STAGED
+        } else if (es == 1) {
             k_bricks<uint8_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint8_t*>(volume->data),
                                                            nx, ny, nz, dtab + first, ghost,
-                                                            rows_per_cta);
-        else if (es == 2)
+                                                           rows_per_cta);
+        } else if (es == 2) {
             k_bricks<uint16_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint16_t*>(volume->data),
                                                             nx, ny, nz, dtab + first, ghost,
                                                             rows_per_cta);
-        else
+        } else {
             k_bricks<uint32_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint32_t*>(volume->data),
                                                             nx, ny, nz, dtab + first, ghost,
                                                             rows_per_cta);
+        }
         e = cudaGetLastError();
         ++launches;
     }
     count_launches(launches);
     if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] brick-decompose %d bricks (%dx%dx%d, ghost %d) grid=(%d,%d) launches=%d\n",
-                numBricks, brickX, brickY, brickZ, ghost, gx, std::min(numBricks, 65535), launches);
+        fprintf(stderr, "[vkt] brick-decompose %d bricks (%dx%dx%d, ghost %d) grid=(%d,%d) %s launches=%d\n",
+                numBricks, brickX, brickY, brickZ, ghost, gx, std::min(numBricks, 65535),
+                staged ? "staged" : "plain", launches);
     const cudaError_t ef = cudaFreeAsync(dtab, ctx.stream);
     if (e == cudaSuccess) e = ef;
     return from_cuda(e);

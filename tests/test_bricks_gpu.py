@@ -31,6 +31,10 @@ def volume(fmt, shape, seed):
     ((33, 20, 65), (64, 8, 11), 3),      # x brick wider than the volume
     ((9, 10, 11), (4, 3, 2), 5),         # ghost wider than a brick
     ((1, 1, 1), (1, 1, 1), 1),
+    ((20, 18, 66), (33, 7, 5), 1),       # rows of odd length: words straddle brick rows
+    ((3, 4, 1500), (700, 2, 2), 1),      # long rows: a row's blocks outnumber a warp's lanes
+    ((20, 18, 64), (16, 8, 8), 0),       # 16-byte aligned spans: block copies
+    ((12, 10, 48), (16, 5, 6), 0),
 ])
 def test_bricks_match_oracle(fmt, shape, brick, ghost):
     src = volume(fmt, shape, SEED + sum(shape) + ghost)
@@ -62,3 +66,26 @@ def test_bricks_of_the_512_volume_reassemble_it():
     # ghosts of an interior brick are the neighbouring voxels of the volume
     b = bricks[(3 * 8 + 4) * 8 + 5]
     assert torch.equal(b, s[3 * 64 - g:4 * 64 + g, 4 * 64 - g:5 * 64 + g, 5 * 64 - g:6 * 64 + g])
+
+
+@pytest.mark.parametrize("fmt", [synth.U8, synth.U16, synth.F32])
+def test_staged_and_plain_paths(fmt, capfd):
+    """A 16-byte aligned source takes the staged kernel; the same voxels one element further
+    into a buffer (not 16-byte aligned) take the plain one.  Both bit-exact."""
+    shape, brick, ghost = (21, 30, 45), (16, 16, 8), 2
+    src = volume(fmt, shape, SEED + 5)
+    ref = oracle.brick_decompose(src, brick, ghost)
+    t = torch.from_numpy(src).cuda()
+    flat = torch.empty(t.numel() + 1, dtype=t.dtype, device="cuda")
+    flat[1:] = t.reshape(-1)
+    shifted = flat[1:].view(shape)
+    for s, path in ((t, "staged"), (shifted, "plain")):
+        capfd.readouterr()
+        with vkt.policy(debug=vkt.DEBUG_LOG):
+            got = vkt.brick_decompose(s, brick, ghost)
+            torch.cuda.synchronize()
+        err = capfd.readouterr().err
+        assert f" {path} " in err, err
+        for i, (g, r) in enumerate(zip(got, ref)):
+            assert np.array_equal(g.cpu().numpy().view(np.uint8),
+                                  np.ascontiguousarray(r).view(np.uint8)), f"{path} brick {i}"

@@ -34,7 +34,8 @@ def check(gpu, ref, t, what):
 
 
 @pytest.mark.parametrize("shape,bricks", [((64, 64, 64), (4, 4, 4)), ((48, 64, 96), (3, 2, 4)),
-                                          ((30, 25, 35), (7, 5, 6)), ((16, 16, 16), (1, 1, 1))])
+                                          ((30, 25, 35), (7, 5, 6)), ((16, 16, 16), (1, 1, 1)),
+                                          ((24, 20, 36), (3, 2, 2))])
 @pytest.mark.parametrize("clip", [0.0, 1.0, 2.0, 40.0])
 def test_clahe_matches_oracle(shape, bricks, clip):
     v = ct_like(shape, SEED + sum(shape))
@@ -44,6 +45,21 @@ def test_clahe_matches_oracle(shape, bricks, clip):
     vkt.synchronize()
     ref, t, _ = oracle.clahe3d(v, bricks, clip)
     check(got.cpu().numpy(), ref, t, f"{shape} bricks {bricks} clip {clip}")
+
+
+@pytest.mark.parametrize("shape,bricks,vec,blend", [((64, 64, 64), (4, 4, 4), 16, "cells"),
+                                                   ((24, 20, 36), (3, 2, 2), 4, "voxels"),
+                                                   ((30, 25, 35), (7, 5, 6), 1, "voxels")])
+def test_clahe_paths(shape, bricks, vec, blend, capfd):
+    """Which histogram load width and which blend kernel a shape takes (each is covered by the
+    parity cases above)."""
+    v = torch.from_numpy(ct_like(shape, SEED)).cuda()
+    capfd.readouterr()
+    with vkt.policy(debug=vkt.DEBUG_LOG):
+        vkt.clahe3d(v, bricks, 2.0)
+        torch.cuda.synchronize()
+    err = capfd.readouterr().err
+    assert f"blend={blend}" in err and f"loads of {vec} bytes" in err, err
 
 
 def test_clahe_paper_size_256():

@@ -316,7 +316,9 @@ VKT_API vktError vktBrickDecomposeCountSV(int32_t* countX, int32_t* countY, int3
  * countX*countY*countZ and ghost >= 0 (else INVALID_VALUE); a brick with the wrong dims gives
  * DIMS_MISMATCH, one with another format, or overlapping the source, INVALID_VALUE.  The
  * bricks must not overlap one another (not checked).  Asynchronous on the policy stream;
- * the brick table is copied into stream-ordered device scratch for the call.
+ * allocates nothing: the bricks' storage pointers are passed to the kernels as launch
+ * parameters (one launch per 3968 bricks), so the caller may reuse the handle array as
+ * soon as the call returns.
  */
 VKT_API vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
                                      vktStructuredVolume volume, int32_t brickX, int32_t brickY,

@@ -13,7 +13,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
-#include <vector>
+#include <memory>
 
 #include "vkt_internal.h"
 
@@ -30,6 +30,36 @@ struct BrickDesc {
     int dx, dy, dz;      // stored dims (interior + 2 ghost)
 };
 
+// The bricks' storage pointers travel as a kernel parameter (no per-call table upload);
+// a launch takes up to MAXB bricks (blockIdx.y), the rest of a brick's description follows
+// from its index in the brick grid.
+constexpr int MAXB = 3968;   // 31.7 KB of pointers, within the 32 KB parameter limit
+struct BrickPtrs {
+    void* p[MAXB];
+};
+struct BrickGrid {
+    int nx, ny, nz;          // volume
+    int bx, by, bz;          // brick size
+    int cx, cy;              // bricks along x and y
+    int first;               // index of the launch's first brick
+    int ghost;
+};
+
+__device__ __forceinline__ BrickDesc brick_at(const BrickPtrs& P, const BrickGrid& G)
+{
+    const int i = G.first + static_cast<int>(blockIdx.y);
+    const int kx = i % G.cx, ky = (i / G.cx) % G.cy, kz = i / (G.cx * G.cy);
+    BrickDesc d;
+    d.dst = P.p[blockIdx.y];
+    d.ox = kx * G.bx;
+    d.oy = ky * G.by;
+    d.oz = kz * G.bz;
+    d.dx = min(G.bx, G.nx - d.ox) + 2 * G.ghost;
+    d.dy = min(G.by, G.ny - d.oy) + 2 * G.ghost;
+    d.dz = min(G.bz, G.nz - d.oz) + 2 * G.ghost;
+    return d;
+}
+
 bool valid_volume(const vktStructuredVolume_impl* v) { return v && v->magic == VKT_VOLUME_MAGIC; }
 
 int elem_bytes(vktDataFormat f) { return f == vktDataFormatUint8 ? 1 : (f == vktDataFormatUint16 ? 2 : 4); }
@@ -43,10 +73,10 @@ constexpr int RP = 4, EPL = 3;
 
 template <typename T>
 __global__ void __launch_bounds__(NT)
-    k_bricks(const T* __restrict__ src, int nx, int ny, int nz, const BrickDesc* __restrict__ bricks,
-             int ghost, int rows_per_cta)
+    k_bricks(const T* __restrict__ src, const BrickPtrs P, const BrickGrid G, int rows_per_cta)
 {
-    const BrickDesc b = bricks[blockIdx.y];
+    const int nx = G.nx, ny = G.ny, nz = G.nz, ghost = G.ghost;
+    const BrickDesc b = brick_at(P, G);
     const int rows = b.dy * b.dz;
     const int r0 = blockIdx.x * rows_per_cta;
     if (r0 >= rows) return;
@@ -138,13 +168,13 @@ __device__ __forceinline__ void cp_async_wait_all()
 // Off: the type of source byte offsets (uint32_t for volumes below 2^31 bytes).
 template <int ES, typename Off>
 __global__ void __launch_bounds__(NT)
-    k_bricks_staged(const unsigned char* __restrict__ src, int nx, int ny, int nz,
-                    uint64_t vol_bytes, const BrickDesc* __restrict__ bricks, int ghost,
-                    int rows_per_cta, int rb, int pitch)
+    k_bricks_staged(const unsigned char* __restrict__ src, uint64_t vol_bytes, const BrickPtrs P,
+                    const BrickGrid G, int rows_per_cta, int rb, int pitch)
 {
     extern __shared__ __align__(16) unsigned char st[];
     __shared__ int s_shift[2][ST_MAXROWS];
-    const BrickDesc b = bricks[blockIdx.y];
+    const int nx = G.nx, ny = G.ny, nz = G.nz, ghost = G.ghost;
+    const BrickDesc b = brick_at(P, G);
     const int rows = b.dy * b.dz;
     const int r0 = blockIdx.x * rows_per_cta;
     if (r0 >= rows) return;
@@ -351,8 +381,8 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     const int es = elem_bytes(volume->format);
     const char* s0 = static_cast<const char*>(volume->data);
     const uint64_t sbytes = static_cast<uint64_t>(nx) * ny * nz * es;
-    std::vector<BrickDesc> desc(static_cast<size_t>(numBricks));
-    int max_rows = 0;
+    int max_rows = 0, pitch = 0;
+    bool staged = (reinterpret_cast<uintptr_t>(volume->data) & 15) == 0;
     for (int kz = 0; kz < cz; ++kz)
         for (int ky = 0; ky < cy; ++ky)
             for (int kx = 0; kx < cx; ++kx) {
@@ -362,7 +392,6 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
                 if (v->format != volume->format) return VKT_ERROR_INVALID_VALUE;
                 const int o[3] = {kx * b[0], ky * b[1], kz * b[2]};
                 const int n[3] = {nx, ny, nz};
-                BrickDesc& d = desc[i];
                 int dd[3];
                 for (int a = 0; a < 3; ++a) dd[a] = std::min(b[a], n[a] - o[a]) + 2 * ghost;
                 if (v->dims[0] != dd[0] || v->dims[1] != dd[1] || v->dims[2] != dd[2])
@@ -370,24 +399,17 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
                 const char* p = static_cast<const char*>(v->data);
                 const uint64_t bytes = static_cast<uint64_t>(dd[0]) * dd[1] * dd[2] * es;
                 if (p < s0 + sbytes && s0 < p + bytes) return VKT_ERROR_INVALID_VALUE;
-                d.dst = v->data;
-                d.ox = o[0];
-                d.oy = o[1];
-                d.oz = o[2];
-                d.dx = dd[0];
-                d.dy = dd[1];
-                d.dz = dd[2];
                 max_rows = std::max(max_rows, dd[1] * dd[2]);
+                // staged kernel: 4-byte aligned bricks; staged bytes per row for the span
+                staged = staged && (reinterpret_cast<uintptr_t>(v->data) & 3) == 0;
+                const int sx0 = o[0] - ghost;
+                const int left = std::min(std::max(-sx0, 0), dd[0]);
+                const int right = std::min(std::max(nx - sx0, left), dd[0]);
+                pitch = std::max(pitch, ((right - left) * es + 30) / 16 * 16 + 16);
             }
     Ctx ctx;
     vktError err = get_context(&ctx);
     if (err != VKT_NO_ERROR) return err;
-    // the brick table lives in stream-ordered scratch for the duration of the call
-    BrickDesc* dtab = nullptr;
-    const size_t tbytes = desc.size() * sizeof(BrickDesc);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&dtab), tbytes, ctx.stream);
-    if (e != cudaSuccess) return from_cuda(e);
-    e = cudaMemcpyAsync(dtab, desc.data(), tbytes, cudaMemcpyHostToDevice, ctx.stream);
     // rows per CTA: enough that the grid is a few waves (short brick rows make small CTAs
     // latency-bound), at least MIN_ROWS_PER_CTA
     int sms = 152;
@@ -399,18 +421,7 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     const int64_t total_rows = static_cast<int64_t>(max_rows) * numBricks;
     const int64_t want = std::max<int64_t>(MIN_ROWS_PER_CTA, total_rows / (static_cast<int64_t>(sms) * 32));
     int rows_per_cta = static_cast<int>(std::min<int64_t>(want, max_rows));
-    // staged kernel: 16-byte aligned source, 4-byte aligned bricks, spans short enough that
-    // a batch holds at least 4 rows
-    bool staged = (reinterpret_cast<uintptr_t>(volume->data) & 15) == 0;
-    int pitch = 0;
-    for (const BrickDesc& d : desc) {
-        staged = staged && (reinterpret_cast<uintptr_t>(d.dst) & 3) == 0;
-        const int sx0 = d.ox - ghost;
-        const int left = std::min(std::max(-sx0, 0), d.dx);
-        const int right = std::min(std::max(nx - sx0, left), d.dx);
-        const int nb = (right - left) * es;
-        pitch = std::max(pitch, (nb + 30) / 16 * 16 + 16);
-    }
+    // staged batches must hold at least 4 rows
     int rb = std::min(ST_MAXROWS, (ST_BUDGET / (2 * std::max(pitch, 1))) & ~3);
     staged = staged && rb >= 4;
     if (staged) {
@@ -418,18 +429,30 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
         rb = std::min(rb, rows_per_cta);
     }
     const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
+    BrickGrid G;
+    G.nx = nx;
+    G.ny = ny;
+    G.nz = nz;
+    G.bx = brickX;
+    G.by = brickY;
+    G.bz = brickZ;
+    G.cx = cx;
+    G.cy = cy;
+    G.ghost = ghost;
+    std::unique_ptr<BrickPtrs> P(new BrickPtrs);
+    cudaError_t e = cudaSuccess;
     int launches = 0;
-    // at most 65535 bricks per launch (grid y)
-    for (int first = 0; e == cudaSuccess && first < numBricks; first += 65535) {
-        const int nb = std::min(65535, numBricks - first);
+    for (int first = 0; e == cudaSuccess && first < numBricks; first += MAXB) {
+        const int nb = std::min(MAXB, numBricks - first);
+        for (int i = 0; i < nb; ++i) P->p[i] = bricks[first + i]->data;
+        G.first = first;
         const dim3 grid(gx, nb);
         const unsigned char* s8 = static_cast<const unsigned char*>(volume->data);
         if (staged) {
             const size_t sm = 2 * static_cast<size_t>(rb) * pitch;
             const bool small = sbytes < (uint64_t(1) << 31);
-#define VKT_BRICKS_STAGED(E, O)                                                                      \
-    k_bricks_staged<E, O><<<grid, NT, sm, ctx.stream>>>(s8, nx, ny, nz, sbytes, dtab + first, ghost, \
-                                                        rows_per_cta, rb, pitch)
+#define VKT_BRICKS_STAGED(E, O) \
+    k_bricks_staged<E, O><<<grid, NT, sm, ctx.stream>>>(s8, sbytes, *P, G, rows_per_cta, rb, pitch)
             if (es == 1) {
                 if (small) VKT_BRICKS_STAGED(1, uint32_t); else VKT_BRICKS_STAGED(1, uint64_t);
             } else if (es == 2) {
@@ -439,16 +462,13 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
             }
 #undef VKT_BRICKS_STAGED
         } else if (es == 1) {
-            k_bricks<uint8_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint8_t*>(volume->data),
-                                                           nx, ny, nz, dtab + first, ghost,
+            k_bricks<uint8_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint8_t*>(volume->data), *P, G,
                                                            rows_per_cta);
         } else if (es == 2) {
-            k_bricks<uint16_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint16_t*>(volume->data),
-                                                            nx, ny, nz, dtab + first, ghost,
+            k_bricks<uint16_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint16_t*>(volume->data), *P, G,
                                                             rows_per_cta);
         } else {
-            k_bricks<uint32_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint32_t*>(volume->data),
-                                                            nx, ny, nz, dtab + first, ghost,
+            k_bricks<uint32_t><<<grid, NT, 0, ctx.stream>>>(static_cast<const uint32_t*>(volume->data), *P, G,
                                                             rows_per_cta);
         }
         e = cudaGetLastError();
@@ -457,10 +477,8 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     count_launches(launches);
     if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] brick-decompose %d bricks (%dx%dx%d, ghost %d) grid=(%d,%d) %s launches=%d\n",
-                numBricks, brickX, brickY, brickZ, ghost, gx, std::min(numBricks, 65535),
+                numBricks, brickX, brickY, brickZ, ghost, gx, std::min(numBricks, MAXB),
                 staged ? "staged" : "plain", launches);
-    const cudaError_t ef = cudaFreeAsync(dtab, ctx.stream);
-    if (e == cudaSuccess) e = ef;
     return from_cuda(e);
 }
 

@@ -89,3 +89,17 @@ def test_staged_and_plain_paths(fmt, capfd):
         for i, (g, r) in enumerate(zip(got, ref)):
             assert np.array_equal(g.cpu().numpy().view(np.uint8),
                                   np.ascontiguousarray(r).view(np.uint8)), f"{path} brick {i}"
+
+
+def test_more_bricks_than_one_launch_takes():
+    """4000 bricks of 1 x 1 x 2 voxels with a ghost cell: the bricks' pointers travel as
+    launch parameters, 3968 per launch, so this call takes two launches."""
+    shape = (20, 20, 20)
+    src = volume(synth.U8, shape, SEED + 77)
+    got = vkt.brick_decompose(torch.from_numpy(src).cuda(), (1, 1, 2), 1)
+    torch.cuda.synchronize()
+    ref = oracle.brick_decompose(src, (1, 1, 2), 1)
+    assert len(got) == len(ref) == 4000
+    g = torch.stack([t.reshape(-1) for t in got]).cpu().numpy()
+    r = np.stack([np.ascontiguousarray(t).reshape(-1) for t in ref])
+    assert np.array_equal(g, r)

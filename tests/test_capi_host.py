@@ -13,6 +13,21 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "vkt.h")
 
 
+def _device_visible():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# The *_without_device tests hand the library fake device addresses and expect each call to
+# stop at argument validation or at the device check.  Where a GPU is visible the device
+# check passes and a kernel would run on those addresses, so they skip there.
+without_device = pytest.mark.skipif(_device_visible(),
+                                    reason="fake device pointers: only where no GPU is visible")
+
+
 @pytest.fixture(scope="module")
 def vkt():
     import paper_2203_10213_gb300 as m
@@ -90,6 +105,7 @@ def test_volume_argument_validation(vkt, lib):
     assert lib.vktStructuredVolumeDestroy(None) == 2
 
 
+@without_device
 def test_apply_filter_validation_without_device(vkt, lib):
     fake1, fake2 = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
     a, b, c = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
@@ -105,6 +121,7 @@ def test_apply_filter_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+@without_device
 def test_apply_filter_range_validation_without_device(vkt, lib):
     fake1, fake2 = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
     a, b = ctypes.c_void_p(), ctypes.c_void_p()
@@ -123,6 +140,7 @@ def test_apply_filter_range_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+@without_device
 def test_brick_decompose_validation_without_device(vkt, lib):
     src = ctypes.c_void_p()
     assert lib.vktStructuredVolumeCreateView(ctypes.byref(src), ctypes.c_void_p(0x100000), 10, 7, 5,
@@ -153,6 +171,7 @@ def test_brick_decompose_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+@without_device
 def test_clahe_validation_without_device(vkt, lib):
     a, b, f = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     assert lib.vktStructuredVolumeCreateView(ctypes.byref(a), ctypes.c_void_p(0x100000), 16, 8, 4,
@@ -172,6 +191,7 @@ def test_clahe_validation_without_device(vkt, lib):
         assert lib.vktStructuredVolumeDestroy(h) == 0
 
 
+@without_device
 def test_render_validation_without_device(vkt, lib):
     import numpy as np
     v = ctypes.c_void_p()

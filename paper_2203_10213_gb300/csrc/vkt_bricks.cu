@@ -165,9 +165,11 @@ __device__ __forceinline__ void cp_async_wait_all()
 // batch's first destination byte is 4-byte aligned; pitch: staged bytes per row (a multiple
 // of 16, at least 16 more than the widest span's covering blocks need).  Shared memory: two
 // buffers of rb x pitch bytes.
-// Off: the type of source byte offsets (uint32_t for volumes below 2^31 bytes).
-template <int ES, typename Off>
-__global__ void __launch_bounds__(NT)
+// Off: the type of source byte offsets (uint32_t for volumes below 2^31 bytes).  BLK: every
+// brick of the launch is written by 16-byte blocks (only that path is compiled in, which
+// keeps registers and so occupancy for it).
+template <int ES, typename Off, bool BLK>
+__global__ void __launch_bounds__(NT, BLK ? 6 : 5)
     k_bricks_staged(const unsigned char* __restrict__ src, uint64_t vol_bytes, const BrickPtrs P,
                     const BrickGrid G, int rows_per_cta, int rb, int pitch)
 {
@@ -212,6 +214,10 @@ __global__ void __launch_bounds__(NT)
     const int lw4 = wpr4 >= 1 && wpr4 <= 32 ? lane - lrow4 * wpr4 : lane;
     const bool words = (L & 3) == 0 && (wpr4 <= 32 ? 4 * rpw4 * wpr4 >= 3 * 32
                                                    : 4 * wpr4 >= 3 * 32 * ((wpr4 + 31) / 32));
+    // 16-byte groups: rows of whole words and a 16-byte aligned brick (batches start at row
+    // multiples of 4, so at multiples of 16 bytes); a thread's groups advance by 16 NT bytes
+    const bool g16 = (L & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+    const int DR16 = (16 * NT) / L, DC16 = (16 * NT) - DR16 * L;
     auto stage = [&](int q0, int nr, int buf) {
         const int boff = buf * rb * pitch;
         const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(st)) + boff;
@@ -265,7 +271,7 @@ __global__ void __launch_bounds__(NT)
         // brick bytes [q0 L, (q0 + nr) L); byte c of batch row rr comes from staged byte
         // pos(c) of that row
         unsigned char* d0 = dst + static_cast<int64_t>(q0) * L;
-        if (v16) {
+        if (BLK || v16) {
             // whole rows, every span 16-byte aligned: 16-byte copies, lanes on (row, block)
             // slots as in the staging
             const uint4* s4 = reinterpret_cast<const uint4*>(st + boff);
@@ -273,6 +279,8 @@ __global__ void __launch_bounds__(NT)
             const int vpr = L >> 4;
             for (int r = warp * rpw16 + lrow16; lrow16 < rpw16 && r < nr; r += NWARP * rpw16)
                 for (int v = lv16; v < vpr; v += 32) d4[r * vpr + v] = s4[(r * pitch >> 4) + v];
+        } else if constexpr (BLK) {
+            // not reached: BLK launches hold only block-copyable bricks
         } else if (words) {
             // rows of whole words, slots keeping at least 3/4 of the lanes busy: lanes on
             // (row, word) slots
@@ -296,6 +304,55 @@ __global__ void __launch_bounds__(NT)
                         }
                     }
                     __stwb(dw + r * wpr + w, v);
+                }
+            }
+        } else if (g16) {
+            // rows of whole words, 16-byte aligned batches: the batch's bytes as one run of
+            // 16-byte groups of four words (a group may span rows, a word may not)
+            const int nbytes = nr * L;
+            uint4* d4 = reinterpret_cast<uint4*>(d0);
+            int rr = (16 * tid) / L, col = 16 * tid - rr * L;
+            for (int g = tid; 16 * g < nbytes; g += NT) {
+                uint32_t v[4];
+                int r = rr, c = col;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (c >= L) {
+                        c -= L;
+                        ++r;
+                    }
+                    v[e] = 0;
+                    if (16 * g + 4 * e < nbytes) {
+                        const int sh = s_sh[r];
+                        if (c >= lb && c + 4 <= rbyte) {
+                            const int bo = r * pitch + sh + (c - lb);
+                            v[e] = __funnelshift_r(sw[bo >> 2], sw[(bo >> 2) + 1],
+                                                   8u * static_cast<uint32_t>(bo & 3));
+                        } else {
+#pragma unroll
+                            for (int b2 = 0; b2 < 4; ++b2) {
+                                const int cb = c + b2;
+                                const int pos = cb < lb ? cb % ES
+                                                        : (cb >= rbyte ? nb - ES + (cb - rbyte) % ES : cb - lb);
+                                v[e] |= uint32_t(st[boff + r * pitch + sh + pos]) << (8 * b2);
+                            }
+                        }
+                    }
+                    c += 4;
+                }
+                if (16 * g + 16 <= nbytes) {
+                    d4[g] = make_uint4(v[0], v[1], v[2], v[3]);
+                } else {
+                    uint32_t* dw = reinterpret_cast<uint32_t*>(d4 + g);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (16 * g + 4 * e < nbytes) __stwb(dw + e, v[e]);
+                }
+                col += DC16;
+                rr += DR16;
+                while (col >= L) {
+                    col -= L;
+                    ++rr;
                 }
             }
         } else {
@@ -429,6 +486,12 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
         rb = std::min(rb, rows_per_cta);
     }
     const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
+    // every brick block-copyable: no ghost cells, rows and brick widths (the last one along x
+    // included) multiples of 16 bytes, bricks 16-byte aligned
+    bool blk = staged && ghost == 0 && (static_cast<int64_t>(nx) * es) % 16 == 0 &&
+               (static_cast<int64_t>(brickX) * es) % 16 == 0 &&
+               (static_cast<int64_t>(nx - (cx - 1) * brickX) * es) % 16 == 0;
+    for (int i = 0; blk && i < numBricks; ++i) blk = (reinterpret_cast<uintptr_t>(bricks[i]->data) & 15) == 0;
     BrickGrid G;
     G.nx = nx;
     G.ny = ny;
@@ -451,8 +514,9 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
         if (staged) {
             const size_t sm = 2 * static_cast<size_t>(rb) * pitch;
             const bool small = sbytes < (uint64_t(1) << 31);
-#define VKT_BRICKS_STAGED(E, O) \
-    k_bricks_staged<E, O><<<grid, NT, sm, ctx.stream>>>(s8, sbytes, *P, G, rows_per_cta, rb, pitch)
+#define VKT_BRICKS_STAGED(E, O)                                                                      \
+    (blk ? k_bricks_staged<E, O, true> : k_bricks_staged<E, O, false>)<<<grid, NT, sm, ctx.stream>>>( \
+        s8, sbytes, *P, G, rows_per_cta, rb, pitch)
             if (es == 1) {
                 if (small) VKT_BRICKS_STAGED(1, uint32_t); else VKT_BRICKS_STAGED(1, uint64_t);
             } else if (es == 2) {
@@ -478,7 +542,7 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] brick-decompose %d bricks (%dx%dx%d, ghost %d) grid=(%d,%d) %s launches=%d\n",
                 numBricks, brickX, brickY, brickZ, ghost, gx, std::min(numBricks, MAXB),
-                staged ? "staged" : "plain", launches);
+                staged ? (blk ? "staged blocks" : "staged") : "plain", launches);
     return from_cuda(e);
 }
 

@@ -103,3 +103,22 @@ def test_more_bricks_than_one_launch_takes():
     g = torch.stack([t.reshape(-1) for t in got]).cpu().numpy()
     r = np.stack([np.ascontiguousarray(t).reshape(-1) for t in ref])
     assert np.array_equal(g, r)
+
+
+@pytest.mark.parametrize("shape,brick,ghost,path", [((20, 18, 64), (16, 8, 8), 0, "staged blocks"),
+                                                    ((20, 18, 64), (16, 8, 8), 1, "staged grid"),
+                                                    ((20, 18, 72), (16, 8, 8), 0, "staged grid")])
+def test_block_only_kernel_when_every_brick_is_aligned(shape, brick, ghost, path, capfd):
+    """Without ghost cells, with 16-byte rows and brick widths (the last brick along x of
+    the 72-wide volume is 8 bytes wide, so that one takes the general kernel), a call runs
+    the kernel that holds only the block copies; results bit-exact either way."""
+    src = volume(synth.U8, shape, SEED + 9)
+    capfd.readouterr()
+    with vkt.policy(debug=vkt.DEBUG_LOG):
+        got = vkt.brick_decompose(torch.from_numpy(src).cuda(), brick, ghost)
+        torch.cuda.synchronize()
+    err = capfd.readouterr().err
+    want = "staged blocks" if path == "staged blocks" else "staged launches"
+    assert want in err, err
+    for g, r in zip(got, oracle.brick_decompose(src, brick, ghost)):
+        assert np.array_equal(g.cpu().numpy(), r)

@@ -414,6 +414,13 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         if (job.roi) kern = k_direct<K, ADJ, -1, -1, LM_ANY, true>;   // reads the region fields
     }
     if constexpr (!ADJ && K >= 3 && K <= 5) {
+        // region tensor-map jobs of the common float32 destinations: formats compiled in
+        if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_U8)
+            kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, true>;
+        if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_F32)
+            kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, true>;
+    }
+    if constexpr (!ADJ && K >= 3 && K <= 5) {
         if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
             if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA>;
             else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS>;

@@ -87,7 +87,8 @@ def clip(box, shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("kind,k", [("dense", 3), ("dense", 5), ("separable", 5), ("separable", 7)])
+@pytest.mark.parametrize("kind,k", [("dense", 3), ("dense", 5), ("separable", 3), ("separable", 5),
+                                    ("separable", 7)])
 @pytest.mark.parametrize("sfmt,dfmt", [(synth.U8, synth.F32), (synth.F32, synth.F32),
                                        (synth.U8, synth.U8), (synth.U16, synth.U16)])
 def test_range_matches_oracle_inside_and_keeps_outside(shape, kind, k, sfmt, dfmt):

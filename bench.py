@@ -71,7 +71,7 @@ KERNEL_CASES = {
 # used only while the sources are unchanged.
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.md")
 KERNEL_SOURCES = {
-    "separable gaussian5": ["vkt_sep_brick.cuh", "vkt_separable.cu", "vkt_tile.cuh"],
+    "separable gaussian5": ["vkt_sep_brick.cuh", "vkt_separable.cuh", "vkt_separable5.cu", "vkt_tile.cuh"],
     "direct laplacian3": ["vkt_direct.cu", "vkt_tile.cuh"],
 }
 

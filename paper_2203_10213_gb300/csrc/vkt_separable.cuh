@@ -112,10 +112,8 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    J.zchunk = sep::choose_zchunk(ex, ey, ez, sms);
     J.tiles_x = (ex + sep::TX - 1) / sep::TX;
     J.tiles_y = (ey + ty - 1) / ty;
-    J.chunks = (ez + J.zchunk - 1) / J.zchunk;
 
     alignas(64) CUtensorMap map;
     J.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz,
@@ -159,6 +157,14 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
+    // z chunks sized for whole waves of the CTAs the chosen kernel keeps resident
+    int per_sm = 0;
+    e = J.comp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, comp, sep::NT, smem)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast, sep::NT, smem);
+    if (e != cudaSuccess) return from_cuda(e);
+    J.zchunk = sep::choose_zchunk(static_cast<long>(J.tiles_x) * J.tiles_y, ez,
+                                  static_cast<long>(sms) * std::max(per_sm, 1), Geo::R);
+    J.chunks = (ez + J.zchunk - 1) / J.zchunk;
     if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] separable%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d\n",
                 J.comp ? "-compensated" : "", K, J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem,

@@ -481,17 +481,44 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     // staged batches must hold at least 4 rows
     int rb = std::min(ST_MAXROWS, (ST_BUDGET / (2 * std::max(pitch, 1))) & ~3);
     staged = staged && rb >= 4;
-    if (staged) {
-        rows_per_cta = (rows_per_cta + 3) & ~3;
-        rb = std::min(rb, rows_per_cta);
-    }
-    const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
     // every brick block-copyable: no ghost cells, rows and brick widths (the last one along x
     // included) multiples of 16 bytes, bricks 16-byte aligned
     bool blk = staged && ghost == 0 && (static_cast<int64_t>(nx) * es) % 16 == 0 &&
                (static_cast<int64_t>(brickX) * es) % 16 == 0 &&
                (static_cast<int64_t>(nx - (cx - 1) * brickX) * es) % 16 == 0;
     for (int i = 0; blk && i < numBricks; ++i) blk = (reinterpret_cast<uintptr_t>(bricks[i]->data) & 15) == 0;
+    const bool small = sbytes < (uint64_t(1) << 31);
+    const void* skern = nullptr;
+    if (staged) {
+#define VKT_PICK(E)                                                                             \
+    skern = small ? (blk ? reinterpret_cast<const void*>(k_bricks_staged<E, uint32_t, true>)    \
+                         : reinterpret_cast<const void*>(k_bricks_staged<E, uint32_t, false>)) \
+                  : (blk ? reinterpret_cast<const void*>(k_bricks_staged<E, uint64_t, true>)    \
+                         : reinterpret_cast<const void*>(k_bricks_staged<E, uint64_t, false>))
+        if (es == 1) VKT_PICK(1); else if (es == 2) VKT_PICK(2); else VKT_PICK(4);
+#undef VKT_PICK
+        // rows per CTA for whole waves of the resident CTAs: the least waves x (rows per CTA
+        // + 32, a CTA's fixed setup counted as rows) over 1 to 64 runs per brick (multiples
+        // of 4 rows, at least MIN_ROWS_PER_CTA)
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, skern, NT,
+                                                          2 * static_cast<size_t>(rb) * pitch) != cudaSuccess)
+            per_sm = 1;
+        const int64_t slots = static_cast<int64_t>(sms) * std::max(per_sm, 1);
+        int64_t best = -1;
+        for (int c = 1; c <= 64; ++c) {
+            const int rpc = std::max(std::min(MIN_ROWS_PER_CTA, (max_rows + 3) & ~3),
+                                     (((max_rows + c - 1) / c) + 3) & ~3);
+            const int64_t ctas = static_cast<int64_t>((max_rows + rpc - 1) / rpc) * numBricks;
+            const int64_t cost = ((ctas + slots - 1) / slots) * (rpc + 32);
+            if (best < 0 || cost < best) {
+                best = cost;
+                rows_per_cta = rpc;
+            }
+        }
+        rb = std::min(rb, rows_per_cta);
+    }
+    const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
     BrickGrid G;
     G.nx = nx;
     G.ny = ny;
@@ -513,7 +540,6 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
         const unsigned char* s8 = static_cast<const unsigned char*>(volume->data);
         if (staged) {
             const size_t sm = 2 * static_cast<size_t>(rb) * pitch;
-            const bool small = sbytes < (uint64_t(1) << 31);
 #define VKT_BRICKS_STAGED(E, O)                                                                      \
     (blk ? k_bricks_staged<E, O, true> : k_bricks_staged<E, O, false>)<<<grid, NT, sm, ctx.stream>>>( \
         s8, sbytes, *P, G, rows_per_cta, rb, pitch)

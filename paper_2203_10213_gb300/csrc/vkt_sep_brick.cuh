@@ -22,7 +22,8 @@ constexpr int NT = 256;
 constexpr int BX = 16, BY = 16;
 constexpr int RX = 4, RY = 2;
 constexpr int TX = BX * RX, TY = BY * RY;
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;    // barriers per CTA; planes in flight of the compensated brick
+constexpr int FSTAGES = 3;   // planes in flight of the float brick (measured faster than 4)
 // How a brick fills its stages, fixed at compile time where the caller knows it (the plane
 // loop is unrolled k times, so code for unused ways costs instruction cache):
 // LM_ANY reads the job's use_tma / rows flags (else plain loads), LM_TMA and LM_ROWS assume one.
@@ -84,7 +85,7 @@ template <int K>
 __host__ __device__ constexpr size_t smem_bytes_fx(int sfmt)
 {
     using Geo = Brick<K, TX, TY>;
-    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, false) +
+    return 128 + static_cast<size_t>(FSTAGES) * Geo::stage_bytes(sfmt, false) +
            2 * static_cast<size_t>(Geo::FH) * TX * sizeof(float);
 }
 
@@ -92,7 +93,7 @@ template <int K>
 __host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 {
     using Geo = Brick<K, TX, TY>;
-    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
+    return 128 + static_cast<size_t>(FSTAGES) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +      // float tile
            static_cast<size_t>(Geo::FH) * TX * sizeof(float);            // x-pass output
 }
@@ -106,7 +107,7 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 }
 
 // Runs brick (bx, by, bz) of job J.  `gplane` counts the planes this CTA has brought in by
-// TMA so far: stage = gplane % STAGES, parity = (gplane / STAGES) & 1, so the ring and its
+// TMA so far: stage = gplane % FSTAGES, parity = (gplane / FSTAGES) & 1, so the ring and its
 // barrier phases carry on across bricks.  Returns false if a bounded wait timed out (after recording it and
 // draining the loads in flight).
 // ROI: the job's region fields (origin, store bounds) are read; otherwise the whole volume is
@@ -131,7 +132,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     constexpr bool FX = fused_x<LM, SF, K>();
-    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+    float* F = reinterpret_cast<float*>(raw + FSTAGES * rawb);
     float* T1 = FX ? F : F + FH * FP;     // FX: two x-pass tiles, no float tile
 
     const int tid = threadIdx.x;
@@ -149,21 +150,21 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const uint64_t vol_bytes =
         static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(sfmt);
     if (tma && tid == 0) {
-        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
+        for (int s = 0; s < FSTAGES && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
-            mbar_arrive_expect_tx(&bars[q % STAGES], txb);
-            tma_load_3d(raw + (q % STAGES) * rawb, tmap, &bars[q % STAGES], x0 - xa, y0 - R,
+            mbar_arrive_expect_tx(&bars[q % FSTAGES], txb);
+            tma_load_3d(raw + (q % FSTAGES) * rawb, tmap, &bars[q % FSTAGES], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
     } else if (rows) {
-        for (int s = 0; s < STAGES && s < nplanes; ++s) {
+        for (int s = 0; s < FSTAGES && s < nplanes; ++s) {
             const uint32_t q = g0 + s;
-            issue_rows<Geo, NT>(raw + (q % STAGES) * rawb, &bars[q % STAGES], J.src, vol_bytes,
+            issue_rows<Geo, NT>(raw + (q % FSTAGES) * rawb, &bars[q % FSTAGES], J.src, vol_bytes,
                                 sfmt, J.nx, J.ny, J.nz, x0, y0, pfirst + s, tid);
         }
         __syncthreads();   // every thread's expect_tx precedes the single arrival
         if (tid == 0)
-            for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % STAGES]);
+            for (int s = 0; s < FSTAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % FSTAGES]);
     }
 
     ConvPlan<Geo, NT> plan;
@@ -197,12 +198,12 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 
     auto plane = [&](const int it, const int u) {
         const uint32_t q = g0 + it;
-        const int s = q % STAGES;
+        const int s = q % FSTAGES;
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
         if constexpr (FX) {
             float* T1b = T1 + (it & 1) * FH * TX;
-            ok = mbar_wait(&bars[s], (q / STAGES) & 1);
+            ok = mbar_wait(&bars[s], (q / FSTAGES) & 1);
             // x pass straight from the raw stage: T1b[row][x] = sum_a gx[a] v(x + a - r), the
             // source voxels converted as they are loaded, clamped in x only at the volume's
             // x faces (the rows are clamped through the stage row read)
@@ -257,15 +258,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
                 failed = true;
                 return;
             }
-            if (tid == 0 && it + STAGES < nplanes) {
+            if (tid == 0 && it + FSTAGES < nplanes) {
                 mbar_arrive_expect_tx(&bars[s], txb);
                 tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
-                            clampi(pfirst + it + STAGES, 0, J.nz - 1));
+                            clampi(pfirst + it + FSTAGES, 0, J.nz - 1));
                 ++issued;
             }
         } else {
         if (tma || rows) {
-            ok = mbar_wait(&bars[s], (q / STAGES) & 1);
+            ok = mbar_wait(&bars[s], (q / FSTAGES) & 1);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, sfmt, J.nx, J.ny,
                                     J.nz, x0, y0, pfirst + it, tid);
@@ -284,15 +285,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             failed = true;
             return;
         }
-        if (tma && tid == 0 && it + STAGES < nplanes) {
+        if (tma && tid == 0 && it + FSTAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(pfirst + it + STAGES, 0, J.nz - 1));
+                        clampi(pfirst + it + FSTAGES, 0, J.nz - 1));
             ++issued;
-        } else if (rows && it + STAGES < nplanes) {
+        } else if (rows && it + FSTAGES < nplanes) {
             // all threads; the arrival follows the x-pass barrier below
             issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, sfmt, J.nx, J.ny,
-                                J.nz, x0, y0, pfirst + it + STAGES, tid);
+                                J.nz, x0, y0, pfirst + it + FSTAGES, tid);
         }
         // x pass: T1[row][x] = sum_a gx[a] F[row][x + a], 4 outputs per item
 #pragma unroll
@@ -316,7 +317,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         }
         __syncthreads();
         // the stage refilled by row copies above is complete in expectation: one arrival
-        if (rows && tid == 0 && it + STAGES < nplanes) {
+        if (rows && tid == 0 && it + FSTAGES < nplanes) {
             mbar_arrive(&bars[s]);
             ++issued;
         }
@@ -423,8 +424,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     if (failed) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);
-            for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
-                mbar_wait(&bars[(g0 + it) % STAGES], ((g0 + it) / STAGES) & 1);
+            for (int it = issued - 1; it >= 0 && it >= issued - FSTAGES; --it)
+                mbar_wait(&bars[(g0 + it) % FSTAGES], ((g0 + it) / FSTAGES) & 1);
         }
         __syncthreads();
         return false;

@@ -483,6 +483,81 @@ def render_form(vkt, torch, stream, src):
             "gsamples_s": round(samples / (ms * 1e-3) / 1e9, 2), "samples": int(samples)}
 
 
+# ------------------------------------------------------------------ differentiation form
+
+def differentiation_form(vkt, torch, stream, lib, dev):
+    """One training step's filter work on a batch of 8 float32 blob volumes of 128^3 with a
+    learnable dense 5^3 kernel (N(0, 0.1)), the loss being the mean squared difference to
+    the same volumes filtered by a hidden 5^3 kernel: the forward filter of each volume
+    (dense direct path), then vktApplyFilterBackwardSV per volume (dL/dx by the exact
+    adjoint, dL/dw by the per-tap reduction with FP64 cross-block sums).  The loss gradient
+    dL/dy = 2 (y - y*) / N is formed between the two by torch (the caller's loss, not the
+    filter) and is not timed.  Reports forward and backward ms per batch, forward+backward
+    Gvoxel/s (output voxels of the forward), and the fraction of the FP32 FMA peak
+    (SMs x 128 FMA per clock x the maximum SM clock) on the algorithmic 3 x 125 FMA per
+    voxel."""
+    import ctypes
+    import synth
+    B, n, k = 8, 128, 5
+    x = torch.from_numpy(np.stack([synth.blobs(synth.BASE_SEED + 100 + b, (n, n, n))
+                                   for b in range(B)]).astype(np.float32)).to(dev)
+    w0 = synth.normal(synth.BASE_SEED + 200, (k, k, k), 0.0, 0.1).astype(np.float32)
+    wh = synth.normal(synth.BASE_SEED + 201, (k, k, k), 0.0, 0.1).astype(np.float32)
+    f, fh = vkt.Filter.dense(w0), vkt.Filter.dense(wh)
+    y, target, gy = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+    gx = torch.zeros_like(x)
+    gw = torch.zeros((B, k ** 3), dtype=torch.float32, device=dev)
+    vx = [vkt.StructuredVolume.from_tensor(x[b]) for b in range(B)]
+    vy = [vkt.StructuredVolume.from_tensor(y[b]) for b in range(B)]
+    vt = [vkt.StructuredVolume.from_tensor(target[b]) for b in range(B)]
+    vgx = [vkt.StructuredVolume.from_tensor(gx[b]) for b in range(B)]
+    vgy = [vkt.StructuredVolume.from_tensor(gy[b]) for b in range(B)]
+    reps = 10
+    fwd_ms, bwd_ms = [], []
+    with vkt.policy(stream=stream, path="direct"):
+        for b in range(B):
+            vkt.check(lib.vktApplyFilterSV(vt[b].handle, vx[b].handle, fh.handle))
+        for it in range(3 + reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            for b in range(B):
+                vkt.check(lib.vktApplyFilterSV(vy[b].handle, vx[b].handle, f.handle))
+            ev[1].record(stream)
+            with torch.cuda.stream(stream):
+                torch.sub(y, target, out=gy)
+                gy.mul_(2.0 / y.numel())
+            ev[2].record(stream)
+            for b in range(B):
+                vkt.check(lib.vktApplyFilterBackwardSV(
+                    vgx[b].handle, ctypes.c_void_p(gw[b].data_ptr()), vgy[b].handle,
+                    vx[b].handle, f.handle))
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            vkt.synchronize()
+            if it >= 3:
+                fwd_ms.append(ev[0].elapsed_time(ev[1]))
+                bwd_ms.append(ev[2].elapsed_time(ev[3]))
+    if not bool(torch.isfinite(gw).all()) or not bool(torch.isfinite(gx).all()):
+        raise RuntimeError("non-finite gradient in the differentiation form")
+    fms, bms = statistics.median(fwd_ms), statistics.median(bwd_ms)
+    vox = B * n ** 3
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = measured_peaks()[0].get("sm_max_mhz", 2070.0)
+    fma_peak = props.multi_processor_count * 128 * sm_mhz * 1e6
+    fma = 3 * k ** 3 * vox
+    for h in vx + vy + vt + vgx + vgy:
+        h.destroy()
+    f.destroy()
+    fh.destroy()
+    return {"batch": B, "dims": [n, n, n], "k": k, "path": "direct (forward), adjoint + weight reduction (backward)",
+            "forward_ms": round(fms, 4), "backward_ms": round(bms, 4),
+            "forward_gvoxel_s": round(vox / (fms * 1e-3) / 1e9, 2),
+            "fwd_bwd_gvoxel_s": round(vox / ((fms + bms) * 1e-3) / 1e9, 2),
+            "fp32_fma_peak_tfma_s": round(fma_peak / 1e12, 1),
+            "frac_fp32": round(fma / ((fms + bms) * 1e-3) / fma_peak, 4),
+            "not_timed": "the loss gradient 2 (y - y*) / N (torch, between forward and backward)"}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -661,7 +736,7 @@ def run_ours(args):
     bform = None
     if not args.no_batching_form:
         bform = batching_form(args, vkt, torch, dev, stream)
-    kform = cform = vform = rform = None
+    kform = cform = vform = rform = dform = None
     if not args.no_extra_forms:
         kform = brick_form(vkt, torch, stream, src)
         cform = clahe_form(vkt, torch, stream)
@@ -669,6 +744,10 @@ def run_ours(args):
         g_roi = vkt.Filter.gaussian(5, 1.5)
         rform = range_form(vkt, torch, stream, lib, v_g, v_l, v_src, g_roi, lap)
         g_roi.destroy()
+        try:
+            dform = differentiation_form(vkt, torch, stream, lib, dev)
+        except Exception as e:   # reported in the line; the step's figures stand on their own
+            dform = {"error": f"{type(e).__name__}: {e}"}
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -682,6 +761,7 @@ def run_ours(args):
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "precision_form": pform, "batching_form": bform,
             "range_form": rform, "brick_form": kform, "clahe_form": cform, "render_form": vform,
+            "differentiation_form": dform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

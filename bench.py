@@ -107,6 +107,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """The largest of every rank's `ms` (the whole job ends when its slowest replica does);
+    an all-reduce over the default process group when world > 1."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_gvoxel_s(voxels_per_step: float, world: int, ms_per_step: float) -> float:
+    """Whole-job output voxels per second (1e9) when each of `world` replicas filters its own
+    volume per step and the job's step takes `ms_per_step` (the slowest rank's)."""
+    return voxels_per_step * world / (ms_per_step * 1e-3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -630,14 +647,10 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in step_ev]
     sep_ms = [e[0].elapsed_time(e[1]) for e in kern_ev]
     dir_ms = [e[1].elapsed_time(e[2]) for e in kern_ev]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev, world)
     ms_per_step = total_ms / K
     vox = float(np.prod(DIMS))
-    value = 2 * vox * world / (ms_per_step * 1e-3) / 1e9
+    value = replica_gvoxel_s(2 * vox, world, ms_per_step)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed.  Steps
     # alternate between two streams, each with its own device volumes and host buffers, so
@@ -687,12 +700,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         vkt.set_policy(stream=stream)
         vkt.synchronize()
-        e2e_ms = a.elapsed_time(b) / E
-        et = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e_ms = float(et.item())
-        e2e = {"value": round(2 * vox * world / (e2e_ms * 1e-3) / 1e9, 3), "unit": "Gvoxel/s",
+        e2e_ms = max_over_ranks(a.elapsed_time(b) / E, dev, world)
+        e2e = {"value": round(replica_gvoxel_s(2 * vox, world, e2e_ms), 3), "unit": "Gvoxel/s",
                "h2d_bytes_per_step": int(host_in.numel()),
                "d2h_bytes_per_step": int(2 * vol.size * 4),
                "ms_per_step": round(e2e_ms, 4),

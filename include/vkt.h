@@ -241,7 +241,9 @@ VKT_API vktError vktApplyFilterRangeSV(vktStructuredVolume dst, vktStructuredVol
  * Batched ApplyFilter over n independent (dst[i], src[i], filters[i]) triples, with
  * the rules of vktApplyFilterSV for each triple, in one persistent launch over a
  * work list of bricks.  The launch is captured in a CUDA graph that is reused while
- * the same handles are passed again.  n >= 1.
+ * the same handles are passed again.  n >= 1.  The triples run at once: a destination
+ * must not overlap another destination or any source of the batch (else INVALID_VALUE);
+ * sources may be shared.
  */
 VKT_API vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
                                vktFilter* filters);

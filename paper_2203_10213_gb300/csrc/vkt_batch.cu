@@ -14,6 +14,7 @@
 // re-uploaded only when weights or value ranges changed.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <list>
@@ -146,6 +147,39 @@ double fqmax(int f) { return f == vktDataFormatUint8 ? 255.0 : 65535.0; }
 uint64_t vbytes(const vktStructuredVolume_impl* v)
 {
     return static_cast<uint64_t>(v->dims[0]) * v->dims[1] * v->dims[2] * fbytes(v->format);
+}
+
+// The triples of a batch run at once, so a destination must be disjoint from every other
+// destination and from every source of the batch (sources may be shared): a write into a
+// volume that another triple reads or writes would have no defined result.  Sorting the
+// destinations makes this O(n log n).
+bool triples_disjoint(int n, const vktStructuredVolume* dst, const vktStructuredVolume* src)
+{
+    struct Span {
+        uintptr_t lo, hi;
+    };
+    std::vector<Span> d;
+    d.reserve(n);
+    for (int i = 0; i < n; ++i) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(dst[i]->data);
+        const uint64_t b = vbytes(dst[i]);
+        if (b) d.push_back({lo, lo + b});
+    }
+    std::sort(d.begin(), d.end(), [](const Span& a, const Span& b) { return a.lo < b.lo; });
+    for (size_t i = 1; i < d.size(); ++i)
+        if (d[i].lo < d[i - 1].hi) return false;
+    for (int j = 0; j < n; ++j) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(src[j]->data);
+        const uint64_t b = vbytes(src[j]);
+        if (!b) continue;
+        const uintptr_t hi = lo + b;
+        // destinations are disjoint and sorted, so their ends rise too: only the last one
+        // that starts below hi can reach past lo
+        auto it = std::lower_bound(d.begin(), d.end(), hi,
+                                   [](const Span& s, uintptr_t v) { return s.lo < v; });
+        if (it != d.begin() && (it - 1)->hi > lo) return false;
+    }
+    return true;
 }
 
 void epilogue_of(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
@@ -380,6 +414,7 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
         const char* ps = static_cast<const char*>(src[i]->data);
         if (pd < ps + vbytes(src[i]) && ps < pd + vbytes(dst[i])) return VKT_ERROR_INVALID_VALUE;
     }
+    if (!triples_disjoint(n, dst, src)) return VKT_ERROR_INVALID_VALUE;
     Ctx ctx;
     vktError err = get_context(&ctx);
     if (err != VKT_NO_ERROR) return err;

@@ -172,6 +172,41 @@ def test_brick_decompose_validation_without_device(vkt, lib):
 
 
 @without_device
+def test_batch_validation_without_device(vkt, lib):
+    """The triples of a batch run at once: no destination may overlap another destination
+    or any source of the batch, while sources may be shared."""
+    nbytes = 8 * 8 * 8 * 4
+
+    def view(addr):
+        h = ctypes.c_void_p()
+        assert lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(addr), 8, 8, 8,
+                                                 vkt.F32, 1, 1, 1, 0, 1) == 0
+        return h
+
+    a, b, c, d = (view(x) for x in (0x100000, 0x200000, 0x300000, 0x400000))
+    touching = view(0x100000 + nbytes)         # starts where a ends: no overlap
+    straddling = view(0x100000 + nbytes - 4)   # shares a's last voxel
+    f = vkt.Filter.gaussian(3, 1.0)
+    arr = lambda *h: (ctypes.c_void_p * len(h))(*(x.value for x in h))
+    B = lambda dst, src: lib.vktApplyFilterBatchSV(len(dst), arr(*dst), arr(*src),
+                                                   arr(*([f.handle] * len(dst))))
+    assert lib.vktApplyFilterBatchSV(0, arr(a), arr(b), arr(f.handle)) == 1
+    assert B([a, c], [b, ctypes.c_void_p()]) == 2   # NULL source handle
+    assert B([a, c], [b, d]) == 6              # valid: reaches the device check
+    assert B([a, c], [b, b]) == 6              # a shared source is fine
+    assert B([a, a], [b, d]) == 1              # one destination written twice
+    assert B([a, c], [b, a]) == 1              # a destination read by another triple
+    assert B([c, a], [a, d]) == 1              # the same, other order
+    assert B([a, touching], [b, d]) == 6
+    assert B([a, straddling], [b, d]) == 1     # destinations overlap by one voxel
+    assert B([c, d], [straddling, b]) == 6     # sources may overlap each other
+    assert B([c, b], [d, straddling]) == 6
+    assert B([straddling, c], [b, a]) == 1     # a destination overlaps another triple's source
+    for h in (a, b, c, d, touching, straddling):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
+@without_device
 def test_clahe_validation_without_device(vkt, lib):
     a, b, f = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     assert lib.vktStructuredVolumeCreateView(ctypes.byref(a), ctypes.c_void_p(0x100000), 16, 8, 4,

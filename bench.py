@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-batching-form", action="store_true",
                     help="skip the 256-volume graph batch vs separate launches comparison")
     ap.add_argument("--no-extra-forms", action="store_true",
-                    help="skip the range, BrickDecompose, CLAHE-3D and render forms")
+                    help="skip the range, BrickDecompose, CLAHE-3D, render, differentiation "
+                         "and smallest-case forms")
     ap.add_argument("--kernel-case", choices=sorted(KERNEL_CASES),
                     help="run one kernel configuration --reps times and exit (for ncu captures)")
     ap.add_argument("--reps", type=int, default=3)
@@ -500,6 +501,55 @@ def render_form(vkt, torch, stream, src):
             "gsamples_s": round(samples / (ms * 1e-3) / 1e9, 2), "samples": int(samples)}
 
 
+# ------------------------------------------------------------------ smallest case
+
+def small_form(vkt, torch, stream, lib, dev):
+    """The smallest case: one float32 volume of 64^3 voxels i.i.d. U[0,1) from the seed, the
+    normalised 3^3 Gaussian sigma 1.0 as dense weights on the FP32 direct path.  Its 2 MiB
+    of algorithmic bytes stay in L2 and one call takes a few microseconds, so it is
+    launch-bound: reported as the per-call time of 200 calls back to back on one stream,
+    and of one call bracketed alone by events (median of 20)."""
+    import oracle
+    import synth
+    n = 64
+    x = torch.from_numpy(synth.volume("uniform", synth.F32, (n, n, n), synth.BASE_SEED)).to(dev)
+    y = torch.empty_like(x)
+    vx, vy = vkt.StructuredVolume.from_tensor(x), vkt.StructuredVolume.from_tensor(y)
+    f = vkt.Filter.dense(oracle.gaussian_weights(3, 1.0).astype(np.float32))
+    loop = 200
+    with vkt.policy(stream=stream, path="direct"):
+        call = lambda: vkt.check(lib.vktApplyFilterSV(vy.handle, vx.handle, f.handle))
+        for _ in range(5):
+            call()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(loop):
+            call()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = a.elapsed_time(b) / loop
+        single = []
+        for _ in range(20):
+            a.record(stream)
+            call()
+            b.record(stream)
+            torch.cuda.synchronize()
+            single.append(a.elapsed_time(b))
+        vkt.synchronize()
+    ms_one = statistics.median(single)
+    vox = n ** 3
+    for h in (vx, vy):
+        h.destroy()
+    f.destroy()
+    return {"dims": [n, n, n], "src": "f32 U[0,1)", "filter": "gaussian k3 sigma1 (dense weights)",
+            "path": "direct", "bound": "launch (inputs and outputs L2-resident)",
+            "back_to_back_ms": round(ms_loop, 5),
+            "back_to_back_gvoxel_s": round(vox / (ms_loop * 1e-3) / 1e9, 2),
+            "single_call_ms": round(ms_one, 5),
+            "single_call_gvoxel_s": round(vox / (ms_one * 1e-3) / 1e9, 2)}
+
+
 # ------------------------------------------------------------------ differentiation form
 
 def differentiation_form(vkt, torch, stream, lib, dev):
@@ -745,7 +795,7 @@ def run_ours(args):
     bform = None
     if not args.no_batching_form:
         bform = batching_form(args, vkt, torch, dev, stream)
-    kform = cform = vform = rform = dform = None
+    kform = cform = vform = rform = dform = sform = None
     if not args.no_extra_forms:
         kform = brick_form(vkt, torch, stream, src)
         cform = clahe_form(vkt, torch, stream)
@@ -757,6 +807,10 @@ def run_ours(args):
             dform = differentiation_form(vkt, torch, stream, lib, dev)
         except Exception as e:   # reported in the line; the step's figures stand on their own
             dform = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            sform = small_form(vkt, torch, stream, lib, dev)
+        except Exception as e:
+            sform = {"error": f"{type(e).__name__}: {e}"}
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "Gvoxel/s", "n_gpus": world,
             "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
@@ -770,7 +824,7 @@ def run_ours(args):
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "precision_form": pform, "batching_form": bform,
             "range_form": rform, "brick_form": kform, "clahe_form": cform, "render_form": vform,
-            "differentiation_form": dform,
+            "differentiation_form": dform, "small_form": sform,
             "wall_s_timed_loop": round(wall, 3)}
     print(json.dumps(line))
     if world > 1:

@@ -12,7 +12,13 @@ kernel, separable kernel = three 1-D clamped passes, hand-derived closed forms o
 volumes (tests/golden), scipy.ndimage.correlate(mode="nearest") and torch float64
 replicate-padded conv3d, the adjoint dot-product identity, and central finite
 differences of a quadratic loss.  ``brick_decompose`` (index arithmetic only, in numpy) is
-pinned by exact reassembly, neighbour agreement and face replication.
+pinned by exact reassembly, neighbour agreement and face replication.  ``clahe3d`` is
+pinned by plain histogram equalisation (one brick, no clip), count conservation under the
+clip limit, brick centres taking their own mapping, scipy's linear interpolation of the
+mappings, and a constant volume.  ``render`` / ``render_pixels`` are pinned by the
+background through a transparent volume, Beer-Lambert attenuation through a uniform slab,
+early termination, linear blending of the lookup table, camera orientation and rays that
+miss the volume.
 """
 from __future__ import annotations
 

@@ -81,3 +81,36 @@ def test_traffic_missing_capture(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "absent.md"))
     assert bench.captured_traffic("direct laplacian3") == (None, "no capture summary")
 
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """The reference arm times the FP64 oracle on the host and prints one JSON line with the
+    same metric and unit as the GPU arm, a cpu_baseline and a zero-copy e2e entry (here on a
+    small stand-in volume and a few hundred voxels per step, to keep the test short)."""
+    import json
+
+    import numpy as np
+    import synth
+    small = synth.volume("blobs", synth.U8, (32, 24, 16), synth.BASE_SEED + 1)
+    monkeypatch.setattr(bench, "workload_host", lambda: small)
+    monkeypatch.setattr(bench, "oracle_sample_rate", lambda vol, seconds: (1e6, 300, 0.1))
+    for var in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(var, raising=False)
+
+    class Args:
+        steps, warmup = 3, 1
+
+    bench.run_reference(Args())
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == "Gvoxel/s"
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1
+    assert d["steps"] == 3 and d["warmup"] == 1
+    assert d["value"] > 0 and np.isfinite(d["value"])
+    assert d["config"]["workload"] == bench.WORKLOAD
+    cpu = d["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["value"] == d["value"] and cpu["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}

@@ -541,3 +541,34 @@ def test_render_camera_orientation():
 def test_render_miss_rays_see_background():
     img = render_uniform(0.5, [[1, 1, 1, 1], [1, 1, 1, 1]], size=(64, 48))
     assert np.allclose(img[0, 0], [0.1, 0.2, 0.3, 0.4])
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("step", [0.5, 0.25])
+def test_render_samples_ramps_at_voxel_centres(axis, step):
+    """Trilinear sampling with voxel centres at i + 0.5: a volume that rises by 1/8 per voxel
+    along one axis is read along the ray as clamp(p - 0.5, 0, 7) / 8, p the ray's coordinate
+    on that axis (exact for a linear ramp; clamped beyond the outer centres).  With a table
+    whose colour equals the value and whose opacity is a constant a, the centre pixel is
+    ac * sum_k (1 - ac)^k s_k + (1 - ac)^K bg, ac = 1 - (1 - a)^step.  An axis mix-up or a
+    half-voxel shift in the sampler changes the result."""
+    n, a = 8, 0.2
+    ramp = np.arange(n, dtype=np.float64) / 8.0
+    shape = [1, 1, 1]
+    shape[2 - axis] = n                               # (z, y, x) array order
+    v = np.broadcast_to(ramp.reshape(shape), (n, n, n)).astype(np.float32).copy()
+    eye = np.array([3.2, 5.9, -20.0])
+    lut = [[0, 0, 0, a], [1, 1, 1, a]]
+    bg = np.array([0.1, 0.2, 0.3, 0.4])
+    # pixel (7, 5) of a 15 x 11 image is the ray along +z through (3.2, 5.9)
+    px = oracle.render(v, 0.0, 1.0, 15, 11, eye, (3.2, 5.9, 4.0), (0, 1, 0), 0.5, step, 2.0,
+                       bg, lut)[5, 7]
+    zs = (np.arange(int(round(n / step))) + 0.5) * step  # sample depths inside [0, 8)
+    p = zs if axis == 2 else np.full_like(zs, eye[axis])
+    s = np.clip(p - 0.5, 0.0, n - 1.0) / 8.0
+    ac = 1.0 - (1.0 - a) ** step
+    trans = (1.0 - ac) ** np.arange(len(zs))
+    C = ac * np.sum(trans * s)
+    A = 1.0 - (1.0 - ac) ** len(zs)
+    assert np.allclose(px[:3], C + (1.0 - A) * bg[:3], atol=1e-12, rtol=0)
+    assert abs(px[3] - (A + (1.0 - A) * bg[3])) < 1e-12

@@ -426,6 +426,34 @@ def test_clahe_single_brick_without_clip_is_histogram_equalisation():
     assert np.array_equal(out, lut[v])
 
 
+def test_clahe_hand_computed_brick_at_the_minimum_limit():
+    """A 2 x 2 x 2 brick of code 10 (N = 8) under clip 1: the limit floor(1 * 8 / 256) = 0
+    is raised to 1 count, so h[10] = 8 keeps 1 and the excess 7 goes back one count each to
+    bins 0, 36, 72, ..., 216 (step 256 // 7 = 36).  Then cdf[10] = h[0] + h[10] = 2 and
+    lut[10] = (255 * 2 + 8 // 2) // 8 = 64, which every voxel takes.  Without a clip limit
+    cdf[10] = 8 and the code maps to 255."""
+    v = np.full((2, 2, 2), 10, np.uint8)
+    out, t, luts = oracle.clahe3d(v, (1, 1, 1), 1.0)
+    assert np.all(out == 64) and np.all(t == 64.0)
+    assert luts[0, 0, 0, 10] == 64
+    assert luts[0, 0, 0].tolist()[:37] == [32] * 10 + [64] * 26 + [96]   # bins 0, 10 and 36
+    out, _, _ = oracle.clahe3d(v, (1, 1, 1), 0.0)
+    assert np.all(out == 255)
+
+
+def test_clahe_exact_ties_round_to_even():
+    """Blends of 2 x 2 bricks of 4 x 4 voxels weigh the mappings by multiples of 1/16, so
+    some land exactly on k + 0.5; the code is then the even neighbour (and otherwise the
+    nearest integer)."""
+    v = np.random.default_rng(1).integers(0, 256, size=(1, 8, 8)).astype(np.uint8)
+    out, t, _ = oracle.clahe3d(v, (2, 2, 1), 0.0)
+    ties = (t - np.floor(t)) == 0.5
+    assert ties.sum() >= 3
+    assert np.all(out[ties] % 2 == 0)
+    assert np.all(np.abs(out[ties].astype(np.float64) - t[ties]) == 0.5)
+    assert np.array_equal(out, np.rint(t).astype(np.uint8))
+
+
 @pytest.mark.parametrize("clip", [0.5, 1.0, 3.0, 40.0])
 def test_clahe_clip_conserves_counts_and_limits_contrast(clip):
     v = synth.quantize(synth.blobs(111, (12, 12, 12), nblobs=3, sigma=(2.0, 5.0)), synth.U8)
@@ -572,3 +600,20 @@ def test_render_samples_ramps_at_voxel_centres(axis, step):
     A = 1.0 - (1.0 - ac) ** len(zs)
     assert np.allclose(px[:3], C + (1.0 - A) * bg[:3], atol=1e-12, rtol=0)
     assert abs(px[3] - (A + (1.0 - A) * bg[3])) < 1e-12
+
+
+def test_render_silhouette_of_a_cube_keeps_square_pixels():
+    """Pinhole projection of an opaque 8^3 cube seen face-on from 20 voxels in front of it:
+    the ray through pixel (px, py) has direction ~ (-sx, sy, 1) with
+    sx = (2 (px + 0.5) / W - 1) tan(fovy/2) W/H and sy = (1 - 2 (py + 0.5) / H) tan(fovy/2),
+    and enters the front face iff |sx| <= 4/20 and |sy| <= 4/20.  With tan(fovy/2) = 0.41
+    on a 40 x 20 image that is columns 15..24 and rows 5..14: a square silhouette, since
+    the horizontal angle per pixel equals the vertical one."""
+    import math
+    v = np.ones((8, 8, 8), np.float32)
+    fovy = 2 * math.atan(0.41)
+    img = oracle.render(v, 0.0, 1.0, 40, 20, (4, 4, -20), (4, 4, 4), (0, 1, 0), fovy, 0.5, 2.0,
+                        (0, 0, 0, 0), [[1, 1, 1, 1], [1, 1, 1, 1]])
+    want = np.zeros((20, 40))
+    want[5:15, 15:25] = 1.0
+    assert np.array_equal(img[..., 3], want)

@@ -617,3 +617,17 @@ def test_render_silhouette_of_a_cube_keeps_square_pixels():
     want = np.zeros((20, 40))
     want[5:15, 15:25] = 1.0
     assert np.array_equal(img[..., 3], want)
+
+
+def test_laplacian_stencil_is_exact_on_quadratics():
+    """The 7-point Laplacian is the exact Laplacian of any quadratic: on
+    f = x^2 + 2 y^2 + 3 z^2 + x y - 4 z + 5 it gives 2 + 4 + 6 = 12 at every interior voxel,
+    and 0 on any linear field; it has 7 non-zero taps summing to 0."""
+    w = oracle.laplacian_3()
+    assert np.count_nonzero(w) == 7 and w.sum() == 0.0
+    z, y, x = np.meshgrid(np.arange(9.0), np.arange(8.0), np.arange(7.0), indexing="ij")
+    f = x ** 2 + 2 * y ** 2 + 3 * z ** 2 + x * y - 4 * z + 5
+    out = oracle.correlate(f.astype(np.float32), w)
+    assert np.allclose(out[1:-1, 1:-1, 1:-1], 12.0, rtol=0, atol=1e-9)
+    lin = (2 * x - 3 * y + 0.5 * z + 1).astype(np.float32)
+    assert np.allclose(oracle.correlate(lin, w)[1:-1, 1:-1, 1:-1], 0.0, rtol=0, atol=1e-9)

@@ -122,6 +122,42 @@ def test_apply_filter_validation_without_device(vkt, lib):
 
 
 @without_device
+def test_backward_validation_without_device(vkt, lib):
+    """vktApplyFilterBackwardSV and its allocation-free weight-gradient variant check their
+    handles, formats, dims, aliasing and the gradient pointer before they need a device."""
+    def view(addr, dims=(8, 8, 8), fmt=None):
+        h = ctypes.c_void_p()
+        assert lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(addr), *dims,
+                                                 vkt.F32 if fmt is None else fmt, 1, 1, 1, 0, 1) == 0
+        return h
+
+    x, gy, gx = view(0x100000), view(0x200000), view(0x300000)
+    other_dims, u8 = view(0x400000, (8, 8, 9)), view(0x500000, fmt=vkt.U8)
+    f = vkt.Filter.gaussian(3, 1.0)
+    gw = ctypes.c_void_p(0x600000)
+    B = lib.vktApplyFilterBackwardSV
+    assert B(gx, gw, None, x, f.handle) == 2
+    assert B(gx, gw, gy, x, None) == 2
+    assert B(gx, gw, gy, u8, f.handle) == 4               # float32 volumes only
+    assert B(gx, gw, other_dims, x, f.handle) == 3
+    assert B(other_dims, gw, gy, x, f.handle) == 3
+    assert B(x, gw, gy, x, f.handle) == 1                 # dL/dx written over the source
+    assert B(gy, gw, gy, x, f.handle) == 1                # ... or over dL/dy
+    assert B(gx, ctypes.c_void_p(0x600002), gy, x, f.handle) == 1   # misaligned dL/dw
+    assert B(gx, gw, gy, x, f.handle) == 6                # valid: reaches the device check
+    assert B(None, gw, gy, x, f.handle) == 6
+    N = lib.vktApplyFilterWeightGradNoAllocSV
+    assert N(gw, None, x, f.handle) == 2
+    assert N(None, gy, x, f.handle) == 1
+    assert N(ctypes.c_void_p(0x600002), gy, x, f.handle) == 1
+    assert N(gw, gy, u8, f.handle) == 4
+    assert N(gw, other_dims, x, f.handle) == 3
+    assert N(gw, gy, x, f.handle) == 6
+    for h in (x, gy, gx, other_dims, u8):
+        assert lib.vktStructuredVolumeDestroy(h) == 0
+
+
+@without_device
 def test_apply_filter_range_validation_without_device(vkt, lib):
     fake1, fake2 = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x200000)
     a, b = ctypes.c_void_p(), ctypes.c_void_p()

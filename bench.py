@@ -218,33 +218,62 @@ def oracle_sample_rate(vol, seconds: float, seed: int = 7):
     return 2 * total_n / total_t, total_n, total_t
 
 
+def cpu_leg(args, vol, pin):
+    """The CPU (oracle) leg, the only part of our arm that runs the oracle: the FP64 oracle
+    timed on the host cores on random voxels of the step's workload (`cpu_baseline`), and
+    the oracle's values at the precision form's sampled voxels, against which that form
+    states the error of each GPU path."""
+    import oracle
+    rate, n, dt = oracle_sample_rate(vol, args.cpu_seconds)
+    cpu = {"value": round(rate / 1e9, 6), "unit": "Gvoxel/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": f"{n} random voxels of the 512^3 volume, both filters, FP64 C, {dt:.1f} s"}
+    refs = None
+    if pin is not None:
+        field, idx, kernels = pin
+        refs = {k: oracle.correlate_points(field, w, idx) for k, (w, _) in kernels.items()}
+    return cpu, refs
+
+
 # ------------------------------------------------------------------ precision form (TC vs FP32)
 
 PF_DIMS = (1024, 1024, 512)
 
 
-def precision_form(args, vkt, torch, dev, stream, peaks):
-    """Split FP16 hi/lo tensor-core path vs plain FP32 path on the 1024x1024x512
-    turbulence-like field with normalised N(0,1) k^3 kernels, k = 7 and 9: Gvoxel/s of
-    each, their ratio, the error of each against the FP64 oracle on sampled voxels, and
-    the tensor pipe's executed FLOP rate against the measured dense FP16/BF16 peak."""
-    import oracle
+def precision_inputs():
+    """The precision form's field, its sampled voxel numbers and its two kernels (k = 7, 9:
+    weights and the seed actually used), all from the seeded generator."""
     import synth
     field = synth.volume("fourier", synth.F32, PF_DIMS, synth.BASE_SEED + 2)
+    idx = np.random.default_rng(5).integers(0, field.size, 20000)
+    kernels = {k: synth.random_kernel(synth.BASE_SEED + 2, k, 1.0, normalise_sum=True)
+               for k in (7, 9)}
+    return field, idx, kernels
+
+
+def precision_form(args, vkt, torch, dev, stream, peaks, field, idx, kernels, refs):
+    """Split FP16 hi/lo tensor-core path vs plain FP32 path on the 1024x1024x512
+    turbulence-like field with normalised N(0,1) k^3 kernels, k = 7 and 9: Gvoxel/s of
+    each, their ratio, the error of each against the FP64 oracle on sampled voxels (the
+    oracle's values `refs` come from the CPU leg, None when it is skipped), and the
+    algorithmic FLOP rate (2 k^3 per voxel) against the measured dense FP16/BF16 tensor
+    peak and against the FP32 CUDA-core peak; the MMA FLOPs the tensor pipe executes
+    (Toeplitz zeros, three split products, N padding) are a separate diagnostic."""
     src = torch.from_numpy(field).to(dev)
     out = torch.empty_like(src)
     v_src = vkt.StructuredVolume.from_tensor(src)
     v_out = vkt.StructuredVolume.from_tensor(out)
     vox = float(np.prod(PF_DIMS))
-    rng = np.random.default_rng(5)
-    idx = rng.integers(0, field.size, 20000)
     xmax = float(np.abs(field).max())
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * measured_peaks()[0].get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     res = {"workload": "fourier 1024x1024x512 f32, normalised N(0,1) kernels", "dims": list(PF_DIMS)}
     for k in (7, 9):
-        w, seed_used = synth.random_kernel(synth.BASE_SEED + 2, k, 1.0, normalise_sum=True)
+        w, seed_used = kernels[k]
         f = vkt.Filter.dense(w)
-        ref = oracle.correlate_points(field, w, idx)
-        scale = oracle.error_scale(w, xmax)
+        ref = refs.get(k) if refs else None
+        # the normalisation of the error: sum|w| * max|x| (float32 weights promoted)
+        scale = float(np.abs(w.astype(np.float64)).sum()) * xmax
         entry = {}
         for path in ("tensor", "direct"):
             with vkt.policy(stream=stream, path=path):
@@ -260,7 +289,7 @@ def precision_form(args, vkt, torch, dev, stream, peaks):
                 vkt.synchronize()
             ms = evs[0].elapsed_time(evs[1]) / args.precision_reps
             got = out.view(-1)[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
-            err = float(np.max(np.abs(got - ref)) / scale)
+            err = float(np.max(np.abs(got - ref)) / scale) if ref is not None else None
             entry[path] = {"ms": round(ms, 4), "gvoxel_s": round(vox / (ms * 1e-3) / 1e9, 2),
                            "max_err_normalised": err}
         # executed tensor FLOPs: per 128 x 16 output voxels and input plane, 2 x-tiles x k
@@ -273,11 +302,15 @@ def precision_form(args, vkt, torch, dev, stream, peaks):
         alg_tflops = 2 * k ** 3 * vox / (tc["ms"] * 1e-3) / 1e12
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         entry["tc_over_fp32"] = round(entry["direct"]["ms"] / tc["ms"], 3)
-        entry["tensor_roofline"] = {"bound": "tensor", "executed_tflops_lower_bound": round(tc_tflops, 1),
-                                    "algorithmic_tflops": round(alg_tflops, 1),
+        entry["tensor_roofline"] = {"bound": "tensor", "achieved": round(alg_tflops, 1),
+                                    "algorithmic_flop_per_voxel": 2 * k ** 3,
                                     "peak": bf16, "unit": "TFLOP/s",
-                                    "frac": round(tc_tflops / bf16, 4),
-                                    "peak_source": "measured bf16_tflops (dense fp16 has the same rate)"}
+                                    "frac": round(alg_tflops / bf16, 4),
+                                    "peak_source": "measured bf16_tflops (dense fp16 has the same rate)",
+                                    "fp32_peak_tflops": round(fp32_peak, 1),
+                                    "frac_vs_fp32_peak": round(alg_tflops / fp32_peak, 4),
+                                    "executed_tflops_lower_bound": round(tc_tflops, 1),
+                                    "executed_frac_diagnostic": round(tc_tflops / bf16, 4)}
         entry["kernel_seed"] = seed_used
         res[f"k{k}"] = entry
     return res
@@ -509,13 +542,15 @@ def small_form(vkt, torch, stream, lib, dev):
     of algorithmic bytes stay in L2 and one call takes a few microseconds, so it is
     launch-bound: reported as the per-call time of 200 calls back to back on one stream,
     and of one call bracketed alone by events (median of 20)."""
-    import oracle
     import synth
     n = 64
     x = torch.from_numpy(synth.volume("uniform", synth.F32, (n, n, n), synth.BASE_SEED)).to(dev)
     y = torch.empty_like(x)
     vx, vy = vkt.StructuredVolume.from_tensor(x), vkt.StructuredVolume.from_tensor(y)
-    f = vkt.Filter.dense(oracle.gaussian_weights(3, 1.0).astype(np.float32))
+    # the library's own normalised Gaussian (its dense float32 weights), given as a dense filter
+    g = vkt.Filter.gaussian(3, 1.0)
+    f = vkt.Filter.dense(g.weights())
+    g.destroy()
     loop = 200
     with vkt.policy(stream=stream, path="direct"):
         call = lambda: vkt.check(lib.vktApplyFilterSV(vy.handle, vx.handle, f.handle))
@@ -635,7 +670,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import oracle
+    import synth
     import paper_2203_10213_gb300 as vkt
 
     dev = torch.device("cuda", local)
@@ -648,7 +683,7 @@ def run_ours(args):
     v_src = vkt.StructuredVolume.from_tensor(src, 0.0, 1.0)
     v_g = vkt.StructuredVolume.from_tensor(out_g, 0.0, 1.0)
     v_l = vkt.StructuredVolume.from_tensor(out_l, 0.0, 1.0)
-    lap = vkt.Filter.dense(oracle.laplacian_3().astype(np.float32))
+    lap = vkt.Filter.dense(synth.laplacian_3())
     lib = vkt._lib
     vkt.set_policy(stream=stream)
 
@@ -781,17 +816,14 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": int(alg_bytes), "traffic": traffic,
                 "traffic_note": traffic_note}
 
-    cpu = None
+    pin = None if args.no_precision_form else precision_inputs()
+    cpu, refs = None, None
     if not args.no_cpu_baseline:
-        import oracle
-        rate, n, dt = oracle_sample_rate(vol, args.cpu_seconds)
-        cpu = {"value": round(rate / 1e9, 6), "unit": "Gvoxel/s", "cores": oracle.num_threads(),
-               "kind": "oracle",
-               "sample": f"{n} random voxels of the 512^3 volume, both filters, FP64 C, {dt:.1f} s"}
+        cpu, refs = cpu_leg(args, vol, pin)
 
     pform = None
-    if not args.no_precision_form:
-        pform = precision_form(args, vkt, torch, dev, stream, peaks)
+    if pin is not None:
+        pform = precision_form(args, vkt, torch, dev, stream, peaks, *pin, refs)
     bform = None
     if not args.no_batching_form:
         bform = batching_form(args, vkt, torch, dev, stream)
@@ -871,7 +903,6 @@ def run_reference(args):
 
 def run_kernel_case(args):
     import torch
-    import oracle
     import synth
     import paper_2203_10213_gb300 as vkt
     kind, fmt, dims, filt, path = KERNEL_CASES[args.kernel_case]
@@ -882,7 +913,7 @@ def run_kernel_case(args):
     if filt == "gaussian5":
         f = vkt.Filter.gaussian(5, 1.5)
     elif filt == "laplacian3":
-        f = vkt.Filter.dense(oracle.laplacian_3().astype(np.float32))
+        f = vkt.Filter.dense(synth.laplacian_3())
     else:
         w, _ = synth.random_kernel(synth.BASE_SEED + 2, 7, 1.0, normalise_sum=True)
         f = vkt.Filter.dense(w)

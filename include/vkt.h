@@ -137,7 +137,11 @@ VKT_API vktError vktStructuredVolumeCreate(vktStructuredVolume* volume, int32_t 
  * Creates a non-owning view of dx*dy*dz voxels at devPtr (for instance the storage of
  * a torch tensor).  devPtr must be aligned to the voxel size and stay valid while the
  * view is used; Destroy never frees it.  Same arguments and errors as Create, plus
- * INVALID_VALUE for a NULL or misaligned devPtr.
+ * INVALID_VALUE for a NULL or misaligned devPtr, and, where a CUDA device is present, for a
+ * devPtr that is neither device memory of the current device nor managed memory (host
+ * memory, pinned or not, or an address no allocation covers; checked with
+ * cudaPointerGetAttributes).  Without a device the pointer is recorded as given, and every
+ * call that would launch a kernel on it returns NO_DEVICE.
  */
 VKT_API vktError vktStructuredVolumeCreateView(vktStructuredVolume* volume, void* devPtr,
                                        int32_t dx, int32_t dy, int32_t dz,
@@ -286,10 +290,11 @@ VKT_API vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gr
  * and it keeps the previous call's contents (each call overwrites all the entries it reads),
  * so calls whose work overlaps on the GPU race: issue them on one stream, or synchronise in
  * between.  Returns VKT_ERROR_INVALID_VALUE when the volume needs more partial sums than the
- * scratch holds (about 64 x 32 voxel tiles times k^3 of them, with the z chunking reduced to
- * fit), VKT_ERROR_UNSUPPORTED for non-float32 volumes, and the errors of
- * vktApplyFilterBackwardSV otherwise.  A bounded device wait that times out is not reported
- * by this call; gradWeights is then undefined.
+ * scratch holds (one per 64 x 32 voxel column tile and z chunk, times k^3), VKT_ERROR_UNSUPPORTED
+ * for non-float32 volumes, and the errors of vktApplyFilterBackwardSV otherwise.  A bounded
+ * device wait that times out is recorded in a status word of this call's own (cleared at the
+ * start of each call, in stream order), not in the one vktSynchronize reads; every entry of
+ * gradWeights is then NaN.
  */
 #define VKT_NOALLOC_SCRATCH_FLOATS (1u << 18)
 VKT_API vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStructuredVolume gradDst,

@@ -170,12 +170,20 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-// dL/dw[d] = sum over CTAs of partials[cta][d], in FP64; one warp per tap
-__global__ void k_wgrad_reduce(const float* partials, int nspatial, int kkk, float* gw)
+// dL/dw[d] = sum over CTAs of partials[cta][d], in FP64; one warp per tap.  `failed`
+// (may be null): a status word that the partial-sum kernel of this call set when a bounded
+// wait of one of its CTAs timed out; that CTA wrote no partials, so the sums would mix in
+// stale scratch, and gw is filled with NaN instead.
+__global__ void k_wgrad_reduce(const float* partials, int nspatial, int kkk, float* gw,
+                               const unsigned* failed)
 {
     const int d = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
     if (d >= kkk) return;
+    if (failed && (*failed & STATUS_TIMEOUT)) {
+        if (lane == 0) gw[d] = __int_as_float(0x7fc00000);
+        return;
+    }
     double s = 0.0;
     for (int i = lane; i < nspatial; i += 32) s += static_cast<double>(partials[static_cast<int64_t>(i) * kkk + d]);
 #pragma unroll
@@ -236,7 +244,8 @@ vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, floa
     e = cudaGetLastError();
     if (e != cudaSuccess) return from_cuda(e);
     const int kkk = K * K * K;
-    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, ctx.stream>>>(partials, static_cast<int>(nspatial), kkk, gw);
+    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, ctx.stream>>>(partials, static_cast<int>(nspatial), kkk, gw,
+                                                         nullptr);
     count_launches(2);
     return from_cuda(cudaGetLastError());
 }
@@ -314,15 +323,13 @@ vktError launch_wg_noalloc(const float* x, const float* gy, int nx, int ny, int 
 {
     using namespace vkt;
     using Geo = Brick<K, TX, TY>;
-    Geometry g = geometry(nx, ny, nz, K);
-    const size_t per_chunk = static_cast<size_t>(g.tiles_x) * g.tiles_y * K * K * K;
-    if (per_chunk > VKT_NOALLOC_SCRATCH_FLOATS) return VKT_ERROR_INVALID_VALUE;
-    const int max_chunks = static_cast<int>(VKT_NOALLOC_SCRATCH_FLOATS / per_chunk);
-    if (g.chunks > max_chunks) {
-        g.zchunk = (nz + max_chunks - 1) / max_chunks;
-        g.chunks = (nz + g.zchunk - 1) / g.zchunk;
-    }
+    // geometry() adds z chunks only while the grid is under about 8 CTAs per SM, so a
+    // volume with more than one chunk needs fewer than 16 x SMs x k^2 partial sums; only
+    // single-chunk volumes of many column tiles can exceed the scratch
+    const Geometry g = geometry(nx, ny, nz, K);
     const int nspatial = g.tiles_x * g.tiles_y * g.chunks;
+    if (static_cast<size_t>(nspatial) * K * K * K > VKT_NOALLOC_SCRATCH_FLOATS)
+        return VKT_ERROR_INVALID_VALUE;
     WgArgs a;
     a.x = x;
     a.gy = gy;
@@ -341,11 +348,14 @@ vktError launch_wg_noalloc(const float* x, const float* gy, int nx, int ny, int 
     cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
+    // the call's own status word starts at zero in stream order (a memset allocates nothing)
+    e = cudaMemsetAsync(status, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return from_cuda(e);
     k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, stream>>>(map, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return from_cuda(e);
     const int kkk = K * K * K;
-    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, nspatial, kkk, gw);
+    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, nspatial, kkk, gw, status);
     count_launches(2);
     return from_cuda(cudaGetLastError());
 }

@@ -365,7 +365,9 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
             for (int t = 0; t < f->k * f->k * f->k; ++t) wsum += f->w[t];
         }
         epilogue_of(dst[i], src[i], wsum, &job.a0, &job.a1, &job.qmax, &job.a0lo, &job.a1lo);
-        job.comp = sepf && separable_needs_comp(dst[i], src[i], f) ? 1 : 0;
+        job.comp = (sepf ? separable_needs_comp(dst[i], src[i], f) : direct_needs_comp(dst[i], src[i], f))
+                       ? 1
+                       : 0;
         if (sepf)
             err = launch_separable(job, f->g[0], f->g[1], f->g[2], f->k, cctx);
         else if (f->k >= 5 && !force_direct && tensor_available(dst[i], src[i], f) == VKT_NO_ERROR)

@@ -1,457 +1,19 @@
-// vkt_direct.cu -- direct FP32 evaluation of ApplyFilter (Sec. 3.2, "Volume Manipulation":
-// a user-specified convolution kernel applied to every cell), all k^3 taps on CUDA cores.
-//
-// Each CTA owns a TX x TY column of output voxels and marches through a chunk of z.  Input
-// planes (with an r-voxel halo) arrive by TMA into a ring of raw tiles, are converted to
-// float with clamp-to-edge into a float tile, and every input plane is multiplied into the
-// K output planes it touches; each thread keeps K x RY x RX accumulators in registers, so
-// an input plane is read from shared memory once per thread window and never again.
-//   K <= 3 : the K accumulator planes rotate by unrolling the plane loop K times;
-//   K >= 5 : they rotate by shifting once per plane (less code for the same arithmetic).
-// Weights travel as kernel parameters and enter the FMAs as constant-bank operands.  For
-// k = 3 the kernel is bound by instruction issue, not by HBM, so there the x taps of each
-// output pair (x, x+1) run as one packed two-lane FMA (half the FMA instructions), and a
-// thread holds 4 rows instead of 2 so the per-plane overhead spreads over 16 outputs.  A
-// slot's first tap in a plane of its z-march (c = b = a = 0) is a plain product, so no
-// accumulator is ever reset.
-//
-// Adjoint mode (ADJ): the same machinery evaluates dL/dx of the clamped correlation.  With
-// the extension E (x_ext(j) = x(clamp(j)) on the domain padded by r), the forward filter is
-// a plain correlation of x_ext, so its adjoint is E^T applied to the zero-padded correlation
-// of gy with the flipped kernel, Z(j') = sum_d w[-d] gy0(j' + d) for j' in [-r, n+r)^3.
-// E^T folds Z onto the volume: gx(j) = sum of Z(j') over the j' whose clamp is j.  The
-// kernel computes Z brick by brick (TMA zero-fills positions outside gy), stores Z
-// directly where j' is strictly inside the volume (exactly one contribution) and
-// atomically adds it to the face voxel clamp(j') everywhere else.
-#include <algorithm>
-#include <cstdio>
-
-#include "vkt_internal.h"
-#include "vkt_tile.cuh"
+// vkt_direct.cu -- the direct kernels with float accumulation (forward, any destination
+// whose FP32 error bound keeps its codes exact, and the adjoint of the backward pass); the
+// kernel template lives in vkt_direct.cuh.
+#include "vkt_direct.cuh"
 
 namespace vkt {
-namespace {
-
-constexpr int NT = 256;          // threads per CTA, 16 x 16
-constexpr int BX = 16, BY = 16;
-constexpr int STAGES = 4;        // raw tiles in flight per CTA
-
-template <int K>
-struct DenseW {
-    float w[K * K * K];
-};
-
-struct DirectArgs {
-    const void* src;
-    void* dst;
-    int nx, ny, nz;
-    int ox0, oy0, oz0;     // origin of the output domain (0, or the padded domain's corner)
-    int ex, ey, ez;        // extent of the output domain
-    int sx0, sx1, sy1;     // forward: voxels with x in [sx0, sx1) and y < sy1 are stored
-    int sfmt, dfmt;
-    int zchunk;
-    int use_tma;
-    int rows;              // no tensor map: stages filled by per-row bulk copies (forward only)
-    int withhold_first;    // fault injection: the first plane's TMA load is never issued
-    float a0, a1, qmax;
-    unsigned* status;
-};
-
-template <int K>
-struct DirectCfg {
-    static constexpr int RX = (K == 9) ? 2 : 4;
-    static constexpr int RY = (K <= 3) ? 4 : 2;
-    static constexpr bool ROT = K >= 5;
-    // PAIR: the x taps run as packed two-lane FMAs over neighbouring outputs (x, x+1),
-    // which halves the FMA instructions of a kernel whose time is instruction issue
-    static constexpr bool PAIR = K == 3;
-    static constexpr int TX = BX * RX, TY = BY * RY;
-    using Geo = Brick<K, TX, TY>;
-};
-
-template <int K>
-__host__ __device__ constexpr size_t direct_smem_bytes(int sfmt, bool rows)
-{
-    using Geo = typename DirectCfg<K>::Geo;
-    return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
-           2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
-}
-
-// Adjoint store of one row of Z values at padded-domain positions (oz, oy, ox + x).
-template <int RX>
-__device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, int nz, int R, int oz,
-                                                  int oy, int ox, const float (&z)[RX])
-{
-    if (oy < -R || oy >= ny + R || oz < -R || oz >= nz + R) return;
-    const int cy = clampi(oy, 0, ny - 1), cz = clampi(oz, 0, nz - 1);
-    const bool inner_yz = oy > 0 && oy < ny - 1 && oz > 0 && oz < nz - 1;
-    const int64_t rowbase = (static_cast<int64_t>(cz) * ny + cy) * nx;
-#pragma unroll
-    for (int x = 0; x < RX; ++x) {
-        const int xx = ox + x;
-        if (xx < -R || xx >= nx + R) continue;
-        const int cx = clampi(xx, 0, nx - 1);
-        if (inner_yz && xx > 0 && xx < nx - 1)
-            dst[rowbase + cx] = z[x];
-        else
-            atomicAdd(dst + rowbase + cx, z[x]);
-    }
-}
-
-// SF/DF: source and destination formats fixed at compile time (-1: read from the arguments);
-// LM: how stages are filled, fixed at compile time where known (the plane loop is unrolled,
-// so code for unused ways of loading costs instruction cache): 0 = from the arguments
-// (tensor map, row copies or plain loads), 1 = tensor map, 2 = row copies
-constexpr int LM_ANY = 0, LM_TMA = 1, LM_ROWS = 2;
-// ROI: the forward stores are bounded by the arguments' region fields; otherwise by the
-// volume (known at compile time to start at column 0)
-template <int K, bool ADJ, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false>
-__global__ void __launch_bounds__(NT)
-    k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
-{
-    using Cfg = DirectCfg<K>;
-    using Geo = typename Cfg::Geo;
-    constexpr int R = Geo::R, RX = Cfg::RX, RY = Cfg::RY;
-    constexpr int FH = Geo::FH, FP = Geo::FP;
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int sfmt = SF >= 0 ? SF : p.sfmt;
-    const int dfmt = DF >= 0 ? DF : p.dfmt;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    const bool tma = LM == LM_TMA || (LM == LM_ANY && p.use_tma);
-    const bool rows = !ADJ && (LM == LM_ROWS || (LM == LM_ANY && p.rows));
-    const int rawb = Geo::stage_bytes(sfmt, rows);
-    const uint32_t txb = Geo::raw_tx(sfmt);
-    unsigned char* raw = smem + 128;
-    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
-
-    const int tid = threadIdx.x;
-    const int tx = tid % BX, ty = tid / BX;
-    const int x0 = p.ox0 + blockIdx.x * Cfg::TX, y0 = p.oy0 + blockIdx.y * Cfg::TY;
-    const int zc0 = p.oz0 + blockIdx.z * p.zchunk;
-    const int zc1 = min(zc0 + p.zchunk, p.oz0 + p.ez);
-    if (zc0 >= zc1) return;
-    const int pfirst = zc0 - R;
-    const int nplanes = zc1 - zc0 + 2 * R;
-    const int xa = fmt_xalign(sfmt);
-
-    if (tid == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-        if (LM != LM_ROWS && p.use_tma) prefetch_tensor_map(&tmap);
-    }
-    __syncthreads();
-    int issued = 0;   // planes handed to the TMA unit so far (thread 0 only)
-    const uint64_t vol_bytes = static_cast<uint64_t>(p.nx) * p.ny * p.nz * fmt_bytes(sfmt);
-    if (tma && tid == 0) {
-        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
-            if (s == 0 && p.withhold_first) continue;
-            mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1));
-        }
-    } else if (rows) {
-        for (int s = 0; s < STAGES && s < nplanes; ++s)
-            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
-                                p.nz, x0, y0, pfirst + s, tid);
-        __syncthreads();   // every thread's expect_tx precedes the single arrival
-        if (tid == 0)
-            for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[s]);
-    }
-    // row copies issued in one plane get their arrival after the next plane's CTA barrier
-    int pend = -1;
-
-    ConvPlan<Geo, NT, !ADJ> plan;
-    plan.init(sfmt, p.nx, p.ny, x0, y0, tid, rows);
-
-    // Accumulators start at zero once; afterwards the first tap a plane's slot receives
-    // (c = 0, b = 0, a = 0) is a plain product, which restarts the slot without a reset.
-    // outputs (x, x+1) of a row share one float2, the operand of the packed FMAs
-    static_assert(RX % 2 == 0, "outputs are paired along x");
-    float2 acc[K][RY][RX / 2];
-#pragma unroll
-    for (int s = 0; s < K; ++s)
-#pragma unroll
-        for (int i = 0; i < RY; ++i)
-#pragma unroll
-            for (int x = 0; x < RX / 2; ++x) acc[s][i][x] = make_float2(0.f, 0.f);
-    auto lane = [&](int s, int i, int x) -> float& {
-        return (x & 1) ? acc[s][i][x >> 1].y : acc[s][i][x >> 1].x;
-    };
-
-    const int ox = x0 + tx * RX;
-    const int nvalid = (ROI ? p.sx1 : p.nx) - ox;
-    const int first = (ROI && p.sx0 > ox) ? p.sx0 - ox : 0;   // leading columns outside the region
-    const int yend = ROI ? p.sy1 : p.ny;
-    bool failed = false;
-
-    // One input plane: fetch, convert, multiply into the K output planes, retire one.
-    auto plane = [&](const int it, const int u) {
-        const int s = it % STAGES;
-        const unsigned char* rs = raw + s * rawb;
-        float* Fb = F + (it & 1) * FH * FP;
-        bool ok = true;
-        if (tma || rows) {
-            ok = mbar_wait(&bars[s], (it / STAGES) & 1);
-        } else {
-            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, sfmt, p.nx,
-                                          p.ny, p.nz, x0, y0, pfirst + it, tid);
-            __syncthreads();
-        }
-        if (ok) {
-            if constexpr (!ADJ) {
-                if (rows) {
-                    const uint32_t zterm =
-                        static_cast<uint32_t>(clampi(pfirst + it, 0, p.nz - 1)) *
-                        static_cast<uint32_t>(p.ny) * static_cast<uint32_t>(p.nx);
-                    plan.convert_rows(rs, sfmt, Fb, tid, p.nx, p.ny, x0, y0, zterm);
-                } else {
-                    plan.convert(rs, sfmt, Fb, tid);
-                }
-            } else {
-                plan.convert(rs, sfmt, Fb, tid);
-            }
-        }
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            return;
-        }
-        if (rows && tid == 0 && pend >= 0) {
-            mbar_arrive(&bars[pend]);
-            ++issued;
-        }
-        pend = -1;
-        if (tma && tid == 0 && it + STAGES < nplanes) {
-            mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1));
-            ++issued;
-        } else if (rows && it + STAGES < nplanes) {
-            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
-                                p.nz, x0, y0, pfirst + it + STAGES, tid);
-            pend = s;
-        }
-        // multiply the plane into the accumulators
-#pragma unroll
-        for (int j = 0; j < RY + K - 1; ++j) {
-            float win[RX + K - 1];
-            load_row<RX + K - 1, RX>(Fb + (ty * RY + j) * FP + tx * RX, win);
-#pragma unroll
-            for (int i = 0; i < RY; ++i) {
-                const int b = j - i;
-                if (b < 0 || b >= K) continue;
-#pragma unroll
-                for (int c = 0; c < K; ++c) {
-                    const int sl = Cfg::ROT ? (K - 1 - c) : (((u - c + R) % K + K) % K);
-                    if constexpr (Cfg::PAIR) {
-#pragma unroll
-                        for (int x = 0; x < RX; x += 2)
-#pragma unroll
-                            for (int a = 0; a < K; ++a) {
-                                const float wv = W.w[(c * K + b) * K + a];
-                                const float2 w2 = make_float2(wv, wv);
-                                const float2 v2 = make_float2(win[x + a], win[x + a + 1]);
-                                float2& d = acc[sl][i][x >> 1];
-                                d = (c == 0 && b == 0 && a == 0) ? __fmul2_rn(w2, v2)
-                                                                 : __ffma2_rn(w2, v2, d);
-                            }
-                    } else {
-#pragma unroll
-                        for (int x = 0; x < RX; ++x)
-#pragma unroll
-                            for (int a = 0; a < K; ++a) {
-                                const float wv = W.w[(c * K + b) * K + a];
-                                float& d = lane(sl, i, x);
-                                d = (c == 0 && b == 0 && a == 0) ? wv * win[x + a]
-                                                                 : fmaf(wv, win[x + a], d);
-                            }
-                    }
-                }
-            }
-        }
-        // output plane it - 2R + zc0 is complete
-        const int sl0 = Cfg::ROT ? 0 : (((u - R) % K + K) % K);
-        if (it >= 2 * R) {
-            const int oz = pfirst + it - R;
-#pragma unroll
-            for (int i = 0; i < RY; ++i) {
-                const int oy = y0 + ty * RY + i;
-                float row[RX];
-#pragma unroll
-                for (int x = 0; x < RX; ++x) row[x] = lane(sl0, i, x);
-                if (ADJ) {
-                    store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
-                                          ox, row);
-                } else if (oy < yend && nvalid > 0) {
-                    const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
-                    store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
-                }
-            }
-        }
-        if (Cfg::ROT) {
-#pragma unroll
-            for (int q = 0; q + 1 < K; ++q)
-#pragma unroll
-                for (int i = 0; i < RY; ++i)
-#pragma unroll
-                    for (int x = 0; x < RX / 2; ++x) acc[q][i][x] = acc[q + 1][i][x];
-        }
-    };
-
-    if (Cfg::ROT) {
-        for (int it = 0; it < nplanes && !failed; ++it) plane(it, 0);
-    } else {
-        for (int g = 0; g * K < nplanes && !failed; ++g) {
-#pragma unroll
-            for (int u = 0; u < K; ++u) {
-                const int it = g * K + u;
-                if (it >= nplanes || failed) break;
-                plane(it, u);
-            }
-        }
-    }
-
-    if (failed) {
-        if (tid == 0) {
-            atomicOr(p.status, STATUS_TIMEOUT);
-            // a refill whose copies are in flight still needs its arrival before the drain
-            if (pend >= 0) {
-                mbar_arrive(&bars[pend]);
-                ++issued;
-            }
-            // drain loads still in flight (bounded) before the CTA's smem is released:
-            // the newest load issued to each stage completes that stage's current phase
-            for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it)
-                if (it != 0 || !p.withhold_first) mbar_wait(&bars[it % STAGES], (it / STAGES) & 1);
-        }
-        __syncthreads();
-    }
-}
-
-template <int K, bool ADJ>
-vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
-{
-    using Cfg = DirectCfg<K>;
-    using Geo = typename Cfg::Geo;
-    constexpr int R = Geo::R;
-    DirectArgs a;
-    a.src = job.src;
-    a.dst = job.dst;
-    a.nx = job.nx;
-    a.ny = job.ny;
-    a.nz = job.nz;
-    a.sfmt = job.sfmt;
-    a.dfmt = job.dfmt;
-    a.a0 = job.a0;
-    a.a1 = job.a1;
-    a.qmax = job.qmax;
-    a.status = ctx.status;
-    a.withhold_first = (ctx.debug & VKT_DEBUG_INJECT_WAIT_TIMEOUT) ? 1 : 0;
-    if (ADJ) {
-        // padded output domain [-r, n+r) per axis; x starts 16 bytes left of the domain
-        // so that every tile's TMA box starts on a 16-byte boundary
-        a.ox0 = -fmt_xalign(job.sfmt);
-        a.oy0 = -R;
-        a.oz0 = -R;
-        a.ex = job.nx + R - a.ox0;
-        a.ey = job.ny + 2 * R;
-        a.ez = job.nz + 2 * R;
-        a.sx0 = 0;
-        a.sx1 = job.nx;
-        a.sy1 = job.ny;
-    } else {
-        // output region; the tiles start on a 16-byte boundary left of it (tensor-map boxes
-        // start there) and store only inside it
-        int rx0, ry0, rz0, rx1, ry1, rz1;
-        job_region(job, rx0, ry0, rz0, rx1, ry1, rz1);
-        a.ox0 = rx0 - rx0 % fmt_xalign(job.sfmt);
-        a.oy0 = ry0;
-        a.oz0 = rz0;
-        a.ex = rx1 - a.ox0;
-        a.ey = ry1 - ry0;
-        a.ez = rz1 - rz0;
-        a.sx0 = rx0;
-        a.sx1 = rx1;
-        a.sy1 = ry1;
-    }
-    DenseW<K> W;
-    const int kk = K * K * K;
-    for (int i = 0; i < kk; ++i) W.w[i] = ADJ ? w[kk - 1 - i] : w[i];   // adjoint: w[-d]
-
-    const int gx = (a.ex + Cfg::TX - 1) / Cfg::TX;
-    const int gy = (a.ey + Cfg::TY - 1) / Cfg::TY;
-    int sms = 152;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
-    const long target = static_cast<long>(sms) * 8;   // ~2 waves of 4 CTAs per SM
-    const long xy = static_cast<long>(gx) * gy;
-    int chunks = static_cast<int>(std::min<long>((target + xy - 1) / xy, std::max(1, a.ez / 8)));
-    chunks = std::max(chunks, 1);
-    a.zchunk = (a.ez + chunks - 1) / chunks;
-    const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
-
-    alignas(64) CUtensorMap map;
-    const int rawx = Geo::raw_w(job.sfmt);
-    a.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz, rawx,
-                                     Geo::FH, 1)
-                    ? 1
-                    : 0;
-    if (!a.use_tma) memset(&map, 0, sizeof(map));
-    // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
-    // per row, when the volume starts on a 16-byte boundary (forward only: the adjoint
-    // needs the zero extension a tensor map or the plain loads give)
-    a.rows = (!ADJ && !a.use_tma && reinterpret_cast<uintptr_t>(job.src) % 16 == 0) ? 1 : 0;
-
-    const size_t smem = direct_smem_bytes<K>(job.sfmt, a.rows != 0);
-    // the common float32 destinations get kernels with their formats compiled in
-    // tensor-map jobs get kernels without the other ways of loading, and so do row-copy
-    // jobs of the compiled-in formats; plain-load jobs take the run-time variant
-    auto kern = a.use_tma ? k_direct<K, ADJ, -1, -1, LM_TMA> : k_direct<K, ADJ, -1, -1, LM_ANY>;
-    if constexpr (!ADJ) {
-        if (job.roi) kern = k_direct<K, ADJ, -1, -1, LM_ANY, true>;   // reads the region fields
-    }
-    if constexpr (!ADJ && K >= 3 && K <= 5) {
-        // region tensor-map jobs of the common float32 destinations: formats compiled in
-        if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_U8)
-            kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, true>;
-        if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_F32)
-            kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, true>;
-    }
-    if constexpr (!ADJ && K >= 3 && K <= 5) {
-        if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
-            if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA>;
-            else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS>;
-        }
-        if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_F32) {
-            if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA>;
-            else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS>;
-        }
-    }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return from_cuda(e);
-    if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d withhold=%d\n",
-                ADJ ? "-adjoint" : "", K, gx, gy, gz, a.zchunk, smem, a.use_tma, a.rows,
-                a.withhold_first);
-    kern<<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
-    count_launches(1);
-    return from_cuda(cudaGetLastError());
-}
-
-}  // namespace
 
 vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx)
 {
+    if (job.comp) return launch_direct_comp(job, w, k, ctx);
     switch (k) {
-    case 1: return launch_k<1, false>(job, w, ctx);
-    case 3: return launch_k<3, false>(job, w, ctx);
-    case 5: return launch_k<5, false>(job, w, ctx);
-    case 7: return launch_k<7, false>(job, w, ctx);
-    case 9: return launch_k<9, false>(job, w, ctx);
+    case 1: return dir::launch_k<1, false>(job, w, ctx);
+    case 3: return dir::launch_k<3, false>(job, w, ctx);
+    case 5: return dir::launch_k<5, false>(job, w, ctx);
+    case 7: return dir::launch_k<7, false>(job, w, ctx);
+    case 9: return dir::launch_k<9, false>(job, w, ctx);
     default: return VKT_ERROR_UNSUPPORTED;
     }
 }
@@ -459,11 +21,11 @@ vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx)
 vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx)
 {
     switch (k) {
-    case 1: return launch_k<1, true>(job, w, ctx);
-    case 3: return launch_k<3, true>(job, w, ctx);
-    case 5: return launch_k<5, true>(job, w, ctx);
-    case 7: return launch_k<7, true>(job, w, ctx);
-    case 9: return launch_k<9, true>(job, w, ctx);
+    case 1: return dir::launch_k<1, true>(job, w, ctx);
+    case 3: return dir::launch_k<3, true>(job, w, ctx);
+    case 5: return dir::launch_k<5, true>(job, w, ctx);
+    case 7: return dir::launch_k<7, true>(job, w, ctx);
+    case 9: return dir::launch_k<9, true>(job, w, ctx);
     default: return VKT_ERROR_UNSUPPORTED;
     }
 }

@@ -39,9 +39,9 @@ struct Job {
     // Epilogue: the kernels accumulate acc = sum w * q over stored source values q and
     // write a0 + a1*acc (float dst), or clamp(rint(a0 + a1*acc), 0, qmax) (integer dst).
     float a0 = 0.f, a1 = 0.f, qmax = 0.f;
-    // Compensated accumulation (separable path, integer destinations): set when an FP32
-    // error bound does not keep the code within 1e-3 LSB of exact; a0lo/a1lo carry the
-    // low halves of a0/a1 as double-float pairs.
+    // Compensated accumulation (integer destinations, direct and separable paths): set when
+    // an FP32 error bound does not keep the code within 5e-4 LSB of exact; a0lo/a1lo carry
+    // the low halves of a0/a1 as double-float pairs.
     int comp = 0;
     float a0lo = 0.f, a1lo = 0.f;
     // Output region of interest (Sec. 3.2, "range" algorithms): when roi is set, only voxels
@@ -69,8 +69,10 @@ struct Ctx {
     unsigned* status;   // device status word of the current device
 };
 
-// Kernel launchers (each returns VKT_NO_ERROR or a launch error).
+// Kernel launchers (each returns VKT_NO_ERROR or a launch error).  launch_direct takes
+// the compensated kernels when job.comp is set (launch_direct_comp).
 vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx);
+vktError launch_direct_comp(const Job& job, const float* w, int k, const Ctx& ctx);
 // dL/dsrc of the clamped correlation (float32 gy in job.src, gx in job.dst; gx must be
 // zeroed first: face voxels are accumulated atomically).
 vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx);
@@ -90,6 +92,9 @@ vktError launch_tensor(const Job& job, const float* w, int k, const Ctx& ctx);
 // Whether a separable filter into an integer destination needs compensated accumulation.
 bool separable_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
                           const vktFilter_impl* f);
+// The same for the direct path with the filter's dense weights.
+bool direct_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                       const vktFilter_impl* f);
 
 // Helpers provided by the runtime.
 vktError get_context(Ctx* ctx);

@@ -169,6 +169,35 @@ bool separable_needs_comp(const vktStructuredVolume_impl* dst, const vktStructur
     return bound >= 5e-4;
 }
 
+// Whether a dense filter into an integer destination needs compensated accumulation.  The
+// direct kernel sums t = sum_d w_d q_d over stored source values q (codes, |q| <= Qs) in
+// k^3 FP32 additions, then forms the code a0 + a1 t with one fma (a1 = (hi_s - lo_s)/Qs * sd,
+// sd = qmax_d / (hi_d - lo_d), both rounded to float32).  With u = 2^-24 the code's error is
+// at most u sd ((k^3 + 1) sum|w| |hi_s - lo_s| + |lo_s| sum|w| + |lo_d|) + u (qmax_d + 1):
+// the sum's k^3 roundings and the rounding of a1 (each relative to sum|w| Qs, scaled by
+// a1), the rounding of a0, and the fma's own.  Below 5e-4 of a code, a rounding decision
+// outside the 1e-3 LSB tie window cannot flip; otherwise the kernel accumulates Dot2
+// pairs.  A float32 source has no known bound on |q| and always takes the compensated
+// kernel.
+bool direct_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                       const vktFilter_impl* f)
+{
+    if (dst->format == vktDataFormatFloat32) return false;
+    if (src->format == vktDataFormatFloat32) return true;
+    const int kkk = f->k * f->k * f->k;
+    double sw = 0.0;
+    for (int i = 0; i < kkk; ++i) sw += std::fabs(static_cast<double>(f->w[i]));
+    const double srange = std::fabs(static_cast<double>(src->hi) - src->lo);
+    const double qd = fmt_qmax(dst->format);
+    const double sd = qd / std::fabs(static_cast<double>(dst->hi) - dst->lo);
+    const double u = std::ldexp(1.0, -24);
+    const double bound = u * sd * ((kkk + 1.0) * sw * srange +
+                                   std::fabs(static_cast<double>(src->lo)) * sw +
+                                   std::fabs(static_cast<double>(dst->lo))) +
+                         u * (qd + 1.0);
+    return bound >= 5e-4;
+}
+
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void uncount_launches(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
@@ -296,6 +325,23 @@ static vktError create_volume(vktStructuredVolume* volume, void* devPtr, int own
     if (err != VKT_NO_ERROR) return err;
     if (!owning && (!devPtr || reinterpret_cast<uintptr_t>(devPtr) % fmt_bytes(format) != 0))
         return VKT_ERROR_INVALID_VALUE;
+    if (!owning && check_device() == VKT_NO_ERROR) {
+        // a view must wrap device memory of the current device (or managed memory): host
+        // memory, or an address no allocation covers, is refused here, before any kernel
+        // could be launched on it
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, devPtr) != cudaSuccess) {
+            cudaGetLastError();
+            return VKT_ERROR_INVALID_VALUE;
+        }
+        int dev = -1;
+        if (cudaGetDevice(&dev) != cudaSuccess) {
+            cudaGetLastError();
+            return VKT_ERROR_NO_DEVICE;
+        }
+        const bool on_device = attr.type == cudaMemoryTypeDevice && attr.device == dev;
+        if (!on_device && attr.type != cudaMemoryTypeManaged) return VKT_ERROR_INVALID_VALUE;
+    }
     auto* v = new (std::nothrow) vktStructuredVolume_impl;
     if (!v) return VKT_ERROR_OUT_OF_MEMORY;
     v->magic = VKT_VOLUME_MAGIC;
@@ -632,6 +678,7 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
     }
     epilogue(dst, src, wsum, &job);
     if (path == VKT_PATH_SEPARABLE) job.comp = separable_needs_comp(dst, src, filter) ? 1 : 0;
+    if (path == VKT_PATH_DIRECT) job.comp = direct_needs_comp(dst, src, filter) ? 1 : 0;
 
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (t_policy.printTimes) {

@@ -436,56 +436,14 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 // ---------------------------------------------------------------------------------------
 // Compensated variant for integer destinations.  An FP32 sum of k taps per pass leaves an
 // error of ~1e-2 of a 16-bit code, more than the 1e-3 LSB within which a rounding tie may
-// go either way, so every pass carries a double-float (hi, lo) value built from error-free
-// transformations: TwoProd(a,b) = (a*b, fma(a,b,-a*b)) and Knuth's TwoSum, accumulated as
-// in the compensated dot product Dot2 (Ogita, Rump, Oishi, "Accurate sum and dot product",
-// SIAM J. Sci. Comput. 2005).  The epilogue maps (hi, lo) to the code value in double-float
-// and takes the rounding decision on the pair.  One output row per thread (RY = 1) keeps the
-// 2 x k x 4 accumulators in registers.
+// go either way, so every pass carries a double-float (hi, lo) value built from the
+// error-free transformations of vkt_tile.cuh (dot2_step, comp_code: the compensated dot
+// product Dot2 of Ogita, Rump and Oishi), and the epilogue takes the rounding decision on
+// the pair.  One output row per thread (RY = 1) keeps the 2 x k x 4 accumulators in
+// registers.
 
 constexpr int CRY = 1;
 constexpr int CTY = BY * CRY;
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (s, c) += g * (h + l), with the product's rounding error recovered exactly
-__device__ __forceinline__ void dot2_step(float g, float h, float l, float& s, float& c)
-{
-    const float p = __fmul_rn(g, h);
-    float e = __fmaf_rn(g, h, -p);
-    e = __fmaf_rn(g, l, e);
-    float t;
-    two_sum(s, p, s, t);
-    c = __fadd_rn(c, __fadd_rn(t, e));
-}
-
-// code = clamp(round-half-even(a0 + a1 * (s + c)), 0, qmax) with a0, a1 double-float
-__device__ __forceinline__ unsigned comp_code(float s, float c, float a0h, float a0l, float a1h,
-                                              float a1l, float qmax)
-{
-    const float p = __fmul_rn(a1h, s);
-    float e = __fmaf_rn(a1h, s, -p);
-    e = __fmaf_rn(a1h, c, e);
-    e = __fmaf_rn(a1l, s, e);
-    float u, t;
-    two_sum(a0h, p, u, t);
-    const float lo = __fadd_rn(__fadd_rn(t, e), a0l);
-    if (!(fabsf(u) < 1.0e9f)) return u > 0.f ? static_cast<unsigned>(qmax) : 0u;   // NaN -> 0
-    float q = rintf(u);
-    const float r = __fadd_rn(__fsub_rn(u, q), lo);   // u - q is exact
-    if (r > 0.5f) q += 1.f;
-    else if (r < -0.5f) q -= 1.f;
-    else if (r == 0.5f || r == -0.5f) {
-        const float cand = r > 0.f ? q + 1.f : q - 1.f;     // exact tie: the even code
-        if (fmodf(cand, 2.f) == 0.f) q = cand;
-    }
-    return static_cast<unsigned>(fminf(fmaxf(q, 0.f), qmax));
-}
 
 template <int K>
 __host__ __device__ constexpr size_t smem_bytes_comp(int sfmt, bool rows = false)

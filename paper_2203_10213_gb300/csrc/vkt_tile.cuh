@@ -416,4 +416,65 @@ __device__ __forceinline__ void store_row(void* dst, int dfmt, int64_t idx, int 
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Error-free transformations for integer destinations whose FP32 rounding error could flip
+// a code: TwoProd(a, b) = (a*b, fma(a, b, -a*b)) and Knuth's TwoSum give each product and
+// each addition with its rounding error exactly, accumulated as in the compensated dot
+// product Dot2 (Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 2005): a running sum s and an error sum c, whose pair (s, c) carries about twice the
+// working precision.
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, c) += g * (h + l), with the product's rounding error recovered exactly
+__device__ __forceinline__ void dot2_step(float g, float h, float l, float& s, float& c)
+{
+    const float p = __fmul_rn(g, h);
+    float e = __fmaf_rn(g, h, -p);
+    e = __fmaf_rn(g, l, e);
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+// (s, c) += g * h for an input h that is exact (a source code or a float32 voxel)
+__device__ __forceinline__ void dot2_exact(float g, float h, float& s, float& c)
+{
+    const float p = __fmul_rn(g, h);
+    const float e = __fmaf_rn(g, h, -p);
+    float t;
+    two_sum(s, p, s, t);
+    c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+// code = clamp(round-half-even(a0 + a1 * (s + c)), 0, qmax) with a0 = a0h + a0l and
+// a1 = a1h + a1l double-float constants: the product and the sum are formed with their
+// rounding errors, and the rounding decision is taken on the pair (u, lo)
+__device__ __forceinline__ unsigned comp_code(float s, float c, float a0h, float a0l, float a1h,
+                                              float a1l, float qmax)
+{
+    const float p = __fmul_rn(a1h, s);
+    float e = __fmaf_rn(a1h, s, -p);
+    e = __fmaf_rn(a1h, c, e);
+    e = __fmaf_rn(a1l, s, e);
+    float u, t;
+    two_sum(a0h, p, u, t);
+    const float lo = __fadd_rn(__fadd_rn(t, e), a0l);
+    if (!(fabsf(u) < 1.0e9f)) return u > 0.f ? static_cast<unsigned>(qmax) : 0u;   // NaN -> 0
+    float q = rintf(u);
+    const float r = __fadd_rn(__fsub_rn(u, q), lo);   // u - q is exact
+    if (r > 0.5f) q += 1.f;
+    else if (r < -0.5f) q -= 1.f;
+    else if (r == 0.5f || r == -0.5f) {
+        const float cand = r > 0.f ? q + 1.f : q - 1.f;     // exact tie: the even code
+        if (fmodf(cand, 2.f) == 0.f) q = cand;
+    }
+    return static_cast<unsigned>(fminf(fmaxf(q, 0.f), qmax));
+}
+
 }  // namespace vkt

@@ -143,6 +143,19 @@ def random_kernel(seed: int, k: int, sd: float = 1.0, normalise_sum: bool = Fals
         s += 1
 
 
+def laplacian_3() -> np.ndarray:
+    """The 3x3x3 kernel of the Laplacian workload as float32 input weights, x fastest: the
+    7-point stencil (centre -6, the six face neighbours +1, the other 20 taps 0).  A
+    literal table: the filter that the GPU arm is given, written independently of the
+    oracle's own copy."""
+    w = np.zeros((3, 3, 3), np.float32)
+    w[1, 1, 1] = -6.0
+    w[0, 1, 1] = w[2, 1, 1] = 1.0
+    w[1, 0, 1] = w[1, 2, 1] = 1.0
+    w[1, 1, 0] = w[1, 1, 2] = 1.0
+    return w
+
+
 # ---------------------------------------------------------------------------------------
 # Workload recipes.  Each returns host numpy arrays; shapes are (nz, ny, nx), x fastest.
 # ---------------------------------------------------------------------------------------

@@ -295,6 +295,31 @@ def test_render_validation_without_device(vkt, lib):
     assert lib.vktStructuredVolumeDestroy(v) == 0
 
 
+@pytest.mark.gpu
+def test_view_refuses_host_memory(vkt, lib):
+    """CreateView checks the pointer it is given: host memory (pageable or pinned) is
+    refused with INVALID_VALUE, device memory of the current device is accepted; the check
+    launches nothing."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    before = vkt.launch_count()
+    host = ctypes.create_string_buffer(4096 + 16)        # pageable host memory
+    addr = (ctypes.addressof(host) + 15) // 16 * 16
+    h = ctypes.c_void_p()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(addr), 16, 16, 16,
+                                             vkt.U8, 1, 1, 1, 0, 1) == 1
+    assert not h.value
+    pinned = torch.empty(4096, dtype=torch.uint8).pin_memory()
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(pinned.data_ptr()),
+                                             16, 16, 16, vkt.U8, 1, 1, 1, 0, 1) == 1
+    dev = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    assert lib.vktStructuredVolumeCreateView(ctypes.byref(h), ctypes.c_void_p(dev.data_ptr()),
+                                             16, 16, 16, vkt.U8, 1, 1, 1, 0, 1) == 0
+    assert lib.vktStructuredVolumeDestroy(h) == 0
+    assert vkt.launch_count() == before
+
+
 def test_owning_create_reports_missing_device(vkt, lib):
     import torch
     if torch.cuda.is_available():

@@ -37,7 +37,7 @@ def test_injected_wait_timeout_is_reported_and_context_recovers():
     # 48 x 32 x 24 uint8 (rows of 48 bytes: tensor-map capable), dense Laplacian, direct path
     vol = synth.volume("blobs", synth.U8, (48, 32, 24), synth.BASE_SEED + 41)
     assert vol.shape == (24, 32, 48)
-    w = oracle.laplacian_3().astype(np.float32)
+    w = synth.laplacian_3()
     filt = vkt.Filter.dense(w)
     src = torch.from_numpy(vol).cuda()
     out = torch.full(vol.shape, -7.0, dtype=torch.float32, device="cuda")

@@ -52,7 +52,7 @@ def test_direct_f32_random_kernel(shape, k):
 
 
 @pytest.mark.parametrize("sfmt", [synth.U8, synth.U16, synth.F32])
-@pytest.mark.parametrize("dfmt", [synth.U8, synth.F32])
+@pytest.mark.parametrize("dfmt", [synth.U8, synth.U16, synth.F32])
 @pytest.mark.parametrize("k", [3, 5])
 def test_direct_format_pairs(sfmt, dfmt, k):
     shape = SHAPES[0] if (sfmt + dfmt) % 2 == 0 else SHAPES[1]
@@ -63,6 +63,36 @@ def test_direct_format_pairs(sfmt, dfmt, k):
     gpu = run_gpu(vkt, src, vkt.Filter.dense(w), DT[dfmt], srange, drange, path="direct")
     ref = oracle.correlate(src, w, *srange)
     compare(gpu, ref, w, src, srange, drange, f"direct {sfmt}->{dfmt} k={k}")
+
+
+@pytest.mark.parametrize("sfmt", [synth.U8, synth.U16, synth.F32])
+@pytest.mark.parametrize("dfmt", [synth.U8, synth.U16])
+def test_direct_laplacian_into_integer_codes(sfmt, dfmt):
+    """The 7-point Laplacian (signed weights) into uint8 / uint16 codes with a shifted
+    destination range: codes bit-exact outside the 1e-3 LSB tie window, negative results
+    clamped to code 0."""
+    shape = SHAPES[(sfmt + dfmt) % 2]
+    src = src_volume(sfmt, shape, SEED + 110 + 3 * sfmt + dfmt)
+    srange, drange = (0.0, 1.0), (-4.0, 9.0)
+    gpu = run_gpu(vkt, src, vkt.Filter.dense(synth.laplacian_3()), DT[dfmt], srange, drange,
+                  path="direct")
+    w = oracle.laplacian_3()
+    ref = oracle.correlate(src, w, *srange)
+    compare(gpu, ref, w, src, srange, drange, f"laplacian {sfmt}->{dfmt}")
+
+
+@pytest.mark.parametrize("k", [3, 5, 7, 9])
+@pytest.mark.parametrize("sfmt", [synth.U16, synth.F32])
+def test_direct_uint16_destination_exact(k, sfmt):
+    """Dense random kernels (N(0.3, 1), not normalised) into uint16 codes with shifted
+    ranges: bit-exact outside the tie window, through the compensated accumulation."""
+    shape = SHAPES[k % 2]
+    src = src_volume(sfmt, shape, SEED + 120 + k + sfmt)
+    w = synth.normal(SEED + 130 + k, (k, k, k), 0.3, 1.0).astype(np.float32)
+    srange, drange = (-1.0, 3.0), (-40.0, 90.0)
+    gpu = run_gpu(vkt, src, vkt.Filter.dense(w), torch.uint16, srange, drange, path="direct")
+    ref = oracle.correlate(src, w, *srange)
+    compare(gpu, ref, w, src, srange, drange, f"dense u16 dst k={k} src {sfmt}")
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -193,7 +223,7 @@ def test_full_size_ct_512_sampled(ct512, which):
         w = oracle.gaussian_weights(5, 1.5)
     else:
         w = oracle.laplacian_3()
-        f = vkt.Filter.dense(w.astype(np.float32))
+        f = vkt.Filter.dense(synth.laplacian_3())
     gpu = run_gpu(vkt, ct512, f, torch.float32)
     idx = _sample_indices(ct512.shape, 200000, SEED + 90)
     ref = oracle.correlate_points(ct512, w, idx, 0.0, 1.0)

@@ -266,6 +266,23 @@ VKT_API vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gr
                                   vktStructuredVolume gradDst, vktStructuredVolume src,
                                   vktFilter filter);
 
+/*
+ * Gradients of a training batch y_b = ApplyFilter(srcs[b], filter), b = 0 .. n-1, one filter
+ * for all volumes (the method's loss over a batch), given gradDsts[b] = dL/dy_b:
+ *   gradSrcs    array of n float32 volumes, or NULL: gradSrcs[b] receives dL/dsrcs[b], the
+ *               exact adjoint of vktApplyFilterBackwardSV;
+ *   gradWeights device float*, k^3, or NULL: receives sum_b dL/dw over the whole batch, every
+ *               volume's per-CTA partial sums reduced together in one FP64 pass.
+ * All volumes are float32 with the dims of srcs[0] (else UNSUPPORTED / DIMS_MISMATCH); no
+ * gradSrcs volume may overlap another one or any gradDsts or srcs volume (INVALID_VALUE).
+ * When each array's volumes lie evenly spaced in memory (as the volumes of one batch tensor
+ * do), dL/dsrc and the partial sums each take one launch over the whole batch; otherwise one
+ * launch per volume, with the one reduction.  Scratch is stream ordered (cudaMallocAsync).
+ */
+VKT_API vktError vktApplyFilterBackwardBatchSV(int32_t n, vktStructuredVolume* gradSrcs,
+                                               float* gradWeights, vktStructuredVolume* gradDsts,
+                                               vktStructuredVolume* srcs, vktFilter filter);
+
 /* ------------------------------------------------------------------ allocation-free variant */
 
 /*

@@ -345,6 +345,23 @@ def apply_filter_backward(grad_src, grad_weights, grad_dst: StructuredVolume,
               "vktApplyFilterBackwardSV")
 
 
+def apply_filter_backward_batch(grad_srcs, grad_weights, grad_dsts, srcs, filt: Filter,
+                                stream=None) -> None:
+    """vktApplyFilterBackwardBatchSV: grad_srcs a list of StructuredVolume or None;
+    grad_weights a float32 CUDA tensor of k^3 entries (dL/dw summed over the batch) or None."""
+    n = len(srcs)
+    if len(grad_dsts) != n or (grad_srcs is not None and len(grad_srcs) != n):
+        raise ValueError("grad_srcs, grad_dsts and srcs must have the same length")
+    arr = ctypes.c_void_p * n
+    gs = arr(*(v.handle.value for v in grad_srcs)) if grad_srcs is not None else None
+    gd = arr(*(v.handle.value for v in grad_dsts))
+    sv = arr(*(v.handle.value for v in srcs))
+    gw = ctypes.c_void_p(grad_weights.data_ptr()) if grad_weights is not None else None
+    with policy(stream=stream):
+        check(_lib.vktApplyFilterBackwardBatchSV(n, gs, gw, gd, sv, filt.handle),
+              "vktApplyFilterBackwardBatchSV")
+
+
 def brick_counts(src: StructuredVolume, brick) -> tuple:
     """(countX, countY, countZ) of vktBrickDecomposeCountSV for brick = (bx, by, bz)."""
     c = [ctypes.c_int32() for _ in range(3)]
@@ -444,38 +461,47 @@ def _autograd_function():
 
     class ApplyFilterFunction(torch.autograd.Function):
         """y = ApplyFilter(x, w) for float32 volumes x of shape (nz, ny, nx) or (B, nz, ny, nx)
-        and a dense k^3 float32 kernel w; backward calls vktApplyFilterBackwardSV (exact
-        adjoint for dL/dx, FP64-reduced dL/dw)."""
+        and a dense k^3 float32 kernel w.  Forward: vktApplyFilterBatchSV with one filter over
+        the batch (one launch on the direct path).  Backward: vktApplyFilterBackwardBatchSV
+        (exact adjoint for dL/dx, dL/dw summed over the batch and reduced in FP64 inside the
+        library).  The kernel reads the weights as launch constants, so the forward copies w
+        to the host once per step; the backward reuses that copy."""
 
         @staticmethod
         def forward(ctx, x, w, path="auto"):
             if x.dtype != torch.float32 or w.dtype != torch.float32:
                 raise TypeError("ApplyFilterFunction takes float32 volumes and weights")
             xb = x.contiguous().reshape((-1,) + tuple(x.shape[-3:]))
-            filt = Filter.dense(w.detach().float().cpu().numpy())
+            w_host = w.detach().float().cpu().numpy()
+            filt = Filter.dense(w_host)
             y = torch.empty_like(xb)
-            for b in range(xb.shape[0]):
-                apply_filter(StructuredVolume.from_tensor(y[b]), StructuredVolume.from_tensor(xb[b]),
-                             filt, path=path)
-            ctx.save_for_backward(xb, w)
+            vx = [StructuredVolume.from_tensor(xb[b]) for b in range(xb.shape[0])]
+            vy = [StructuredVolume.from_tensor(y[b]) for b in range(xb.shape[0])]
+            with policy(path=path):
+                apply_filter_batch(vy, vx, [filt] * len(vx))
+            ctx.save_for_backward(xb)
+            ctx.filt = filt
+            ctx.w_shape = w.shape
             ctx.shape = x.shape
             return y.reshape(x.shape)
 
         @staticmethod
         def backward(ctx, gy):
-            xb, w = ctx.saved_tensors
+            (xb,) = ctx.saved_tensors
             gyb = gy.contiguous().reshape(xb.shape)
-            filt = Filter.dense(w.detach().float().cpu().numpy())
             need_x, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
             gx = torch.empty_like(xb) if need_x else None
-            gws = torch.empty((xb.shape[0], w.numel()), dtype=torch.float32, device=xb.device) if need_w else None
-            for b in range(xb.shape[0]):
-                apply_filter_backward(StructuredVolume.from_tensor(gx[b]) if need_x else None,
-                                      gws[b] if need_w else None,
-                                      StructuredVolume.from_tensor(gyb[b]),
-                                      StructuredVolume.from_tensor(xb[b]), filt)
-            gw = gws.sum(0).reshape(w.shape) if need_w else None
-            return (gx.reshape(ctx.shape) if need_x else None), gw, None
+            k3 = 1
+            for d in ctx.w_shape:
+                k3 *= d
+            gw = torch.empty(k3, dtype=torch.float32, device=xb.device) if need_w else None
+            n = xb.shape[0]
+            apply_filter_backward_batch(
+                [StructuredVolume.from_tensor(gx[b]) for b in range(n)] if need_x else None, gw,
+                [StructuredVolume.from_tensor(gyb[b]) for b in range(n)],
+                [StructuredVolume.from_tensor(xb[b]) for b in range(n)], ctx.filt)
+            return ((gx.reshape(ctx.shape) if need_x else None),
+                    (gw.reshape(ctx.w_shape) if need_w else None), None)
 
     return ApplyFilterFunction
 

@@ -64,6 +64,7 @@ SIGNATURES = {
     "vktRenderSV": [p, i32, i32, p, p],
     "vktApplyFilterBatchSV": [i32, ctypes.POINTER(p), ctypes.POINTER(p), ctypes.POINTER(p)],
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
+    "vktApplyFilterBackwardBatchSV": [i32, ctypes.POINTER(p), p, ctypes.POINTER(p), ctypes.POINTER(p), p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],
 }
 

@@ -27,9 +27,10 @@ constexpr int STAGES = 4;
 struct WgArgs {
     const float* x;
     const float* gy;
-    float* partials;     // [nspatial][k^3]
+    float* partials;     // [nspatial][k^3], nspatial = volumes x chunks x tiles_y x tiles_x
     int nx, ny, nz;
-    int tiles_x, tiles_y, zchunk;
+    int tiles_x, tiles_y, zchunk, chunks;
+    int64_t vs_x, vs_gy; // voxels from one volume of the batch to the next
     int use_tma;
     unsigned* status;
 };
@@ -62,7 +63,11 @@ __global__ void __launch_bounds__(NT)
     const int c = blockIdx.x % K;
     const int xt = blockIdx.x / K;
     const int x0 = xt * TX, y0 = blockIdx.y * TY;
-    const int zc0 = blockIdx.z * p.zchunk;
+    // blockIdx.z = volume * chunks + z chunk
+    const int vol = static_cast<int>(blockIdx.z) / p.chunks;
+    const int zc0 = (static_cast<int>(blockIdx.z) - vol * p.chunks) * p.zchunk;
+    const float* xv = p.x + vol * p.vs_x;
+    const float* gyv = p.gy + vol * p.vs_gy;
     const int zc1 = min(zc0 + p.zchunk, p.nz);
     const int nplanes = max(zc1 - zc0, 0);
     constexpr int xa = 4;     // float32 x halo that keeps the TMA box 16-byte aligned
@@ -78,8 +83,8 @@ __global__ void __launch_bounds__(NT)
     if (p.use_tma && tid == 0) {
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(zc0 + s + c - R, 0, p.nz - 1));
+            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(zc0 + s + c - R, 0, p.nz - 1), vol);
         }
     }
     ConvPlan<Geo, NT> plan;
@@ -107,12 +112,12 @@ __global__ void __launch_bounds__(NT)
             const int64_t row = (static_cast<int64_t>(z) * p.ny + oy) * p.nx;
 #pragma unroll
             for (int x = 0; x < RX; ++x)
-                g[i][x] = (oy < p.ny && ox + x < p.nx) ? __ldg(p.gy + row + ox + x) : 0.f;
+                g[i][x] = (oy < p.ny && ox + x < p.nx) ? __ldg(gyv + row + ox + x) : 0.f;
         }
         if (p.use_tma) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
-            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), p.x, FMT_F32,
+            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), xv, FMT_F32,
                                     p.nx, p.ny, p.nz, x0, y0, z + c - R, tid);
             __syncthreads();
         }
@@ -123,8 +128,8 @@ __global__ void __launch_bounds__(NT)
         }
         if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(zc0 + it + STAGES + c - R, 0, p.nz - 1));
+            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        clampi(zc0 + it + STAGES + c - R, 0, p.nz - 1), vol);
             ++issued;
         }
 #pragma unroll
@@ -195,7 +200,10 @@ struct Geometry {
     int tiles_x, tiles_y, chunks, zchunk;
 };
 
-Geometry geometry(int nx, int ny, int nz, int k)
+// CTAs: k kernel planes x tiles_x x tiles_y x chunks per volume, the z chunks chosen by
+// zchunk_for over all volumes' tiles (at least 8 planes per chunk unless the job is too
+// small for one CTA per SM).
+Geometry geometry(int nx, int ny, int nz, int k, int nvol = 1)
 {
     Geometry g;
     g.tiles_x = (nx + TX - 1) / TX;
@@ -203,22 +211,20 @@ Geometry geometry(int nx, int ny, int nz, int k)
     int sms = 152, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long target = static_cast<long>(sms) * 8;
-    const long xyc = static_cast<long>(g.tiles_x) * g.tiles_y * k;
-    g.chunks = static_cast<int>(std::max<long>(1, std::min<long>((target + xyc - 1) / xyc, std::max(1, nz / 8))));
-    g.zchunk = (nz + g.chunks - 1) / g.chunks;
+    const long xyc = static_cast<long>(g.tiles_x) * g.tiles_y * k * std::max(nvol, 1);
+    g.zchunk = zchunk_for(xyc, nz, sms);
     g.chunks = (nz + g.zchunk - 1) / g.zchunk;
     return g;
 }
 
+// The partial-sum kernel over nvol volumes (vs_x, vs_gy voxels apart) into `partials`.
 template <int K>
-vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, float* partials,
-                   size_t cap, float* gw, const Ctx& ctx)
+vktError launch_wg_partials(const float* x, const float* gy, int nx, int ny, int nz, int nvol,
+                            int64_t vs_x, int64_t vs_gy, const Geometry& g, float* partials,
+                            unsigned* status, cudaStream_t stream, int debug)
 {
     using Geo = Brick<K, TX, TY>;
-    const Geometry g = geometry(nx, ny, nz, K);
-    const size_t nspatial = static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks;
-    if (nspatial * K * K * K > cap) return VKT_ERROR_INVALID_VALUE;
+    if (static_cast<long>(g.chunks) * nvol > 65535) return VKT_ERROR_UNSUPPORTED;
     WgArgs a;
     a.x = x;
     a.gy = gy;
@@ -229,46 +235,92 @@ vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, floa
     a.tiles_x = g.tiles_x;
     a.tiles_y = g.tiles_y;
     a.zchunk = g.zchunk;
-    a.status = ctx.status;
+    a.chunks = g.chunks;
+    a.vs_x = vs_x;
+    a.vs_gy = vs_gy;
+    a.status = status;
     alignas(64) CUtensorMap map;
-    a.use_tma = encode_tensor_map_3d(&map, FMT_F32, x, nx, ny, nz, Geo::raw_w(FMT_F32), Geo::FH, 1) ? 1 : 0;
+    a.use_tma = encode_tensor_map(&map, FMT_F32, x, nx, ny, nz, nvol, vs_x, Geo::raw_w(FMT_F32),
+                                  Geo::FH, 1)
+                    ? 1
+                    : 0;
     if (!a.use_tma) memset(&map, 0, sizeof(map));
     const size_t smem = wgrad_smem_bytes<K>();
     cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
-    if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] wgrad k=%d grid=(%d,%d,%d) zchunk=%d tma=%d\n", K, g.tiles_x * K,
-                g.tiles_y, g.chunks, g.zchunk, a.use_tma);
-    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, ctx.stream>>>(map, a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return from_cuda(e);
-    const int kkk = K * K * K;
-    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, ctx.stream>>>(partials, static_cast<int>(nspatial), kkk, gw,
-                                                         nullptr);
-    count_launches(2);
+    if (debug & VKT_DEBUG_LOG)
+        fprintf(stderr, "[vkt] wgrad k=%d grid=(%d,%d,%d) zchunk=%d volumes=%d tma=%d\n", K,
+                g.tiles_x * K, g.tiles_y, g.chunks * nvol, g.zchunk, nvol, a.use_tma);
+    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks * nvol), NT, smem, stream>>>(map, a);
+    count_launches(1);
+    return from_cuda(cudaGetLastError());
+}
+
+void launch_reduce(const float* partials, size_t nspatial, int k, float* gw, const unsigned* failed,
+                   cudaStream_t stream)
+{
+    const int kkk = k * k * k;
+    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, static_cast<int>(nspatial), kkk, gw,
+                                                       failed);
+    count_launches(1);
+}
+
+template <int K>
+vktError launch_wg(const float* x, const float* gy, int nx, int ny, int nz, float* partials,
+                   size_t cap, float* gw, const Ctx& ctx, int nvol, int64_t vs_x, int64_t vs_gy)
+{
+    const Geometry g = geometry(nx, ny, nz, K, nvol);
+    const size_t nspatial = static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks * nvol;
+    if (nspatial * K * K * K > cap) return VKT_ERROR_INVALID_VALUE;
+    vktError err = launch_wg_partials<K>(x, gy, nx, ny, nz, nvol, vs_x, vs_gy, g, partials,
+                                         ctx.status, ctx.stream, ctx.debug);
+    if (err != VKT_NO_ERROR) return err;
+    launch_reduce(partials, nspatial, K, gw, nullptr, ctx.stream);
     return from_cuda(cudaGetLastError());
 }
 
 }  // namespace
 
-size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k)
+size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k, int nvol)
 {
-    const Geometry g = geometry(nx, ny, nz, k);
-    return static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks * k * k * k;
+    const Geometry g = geometry(nx, ny, nz, k, nvol);
+    return static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks * std::max(nvol, 1) * k * k * k;
 }
 
 vktError launch_weight_grad(const float* x, const float* gy, int nx, int ny, int nz, int k,
-                            float* partials, size_t cap, float* gw, const Ctx& ctx)
+                            float* partials, size_t cap, float* gw, const Ctx& ctx, int nvol,
+                            int64_t vs_x, int64_t vs_gy)
 {
+    nvol = std::max(nvol, 1);
     switch (k) {
-    case 1: return launch_wg<1>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
-    case 3: return launch_wg<3>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
-    case 5: return launch_wg<5>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
-    case 7: return launch_wg<7>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
-    case 9: return launch_wg<9>(x, gy, nx, ny, nz, partials, cap, gw, ctx);
+    case 1: return launch_wg<1>(x, gy, nx, ny, nz, partials, cap, gw, ctx, nvol, vs_x, vs_gy);
+    case 3: return launch_wg<3>(x, gy, nx, ny, nz, partials, cap, gw, ctx, nvol, vs_x, vs_gy);
+    case 5: return launch_wg<5>(x, gy, nx, ny, nz, partials, cap, gw, ctx, nvol, vs_x, vs_gy);
+    case 7: return launch_wg<7>(x, gy, nx, ny, nz, partials, cap, gw, ctx, nvol, vs_x, vs_gy);
+    case 9: return launch_wg<9>(x, gy, nx, ny, nz, partials, cap, gw, ctx, nvol, vs_x, vs_gy);
     default: return VKT_ERROR_UNSUPPORTED;
     }
+}
+
+vktError launch_weight_grad_partials(const float* x, const float* gy, int nx, int ny, int nz,
+                                     int k, float* partials, const Ctx& ctx)
+{
+    const Geometry g = geometry(nx, ny, nz, k, 1);
+    switch (k) {
+    case 1: return launch_wg_partials<1>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, ctx.status, ctx.stream, ctx.debug);
+    case 3: return launch_wg_partials<3>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, ctx.status, ctx.stream, ctx.debug);
+    case 5: return launch_wg_partials<5>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, ctx.status, ctx.stream, ctx.debug);
+    case 7: return launch_wg_partials<7>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, ctx.status, ctx.stream, ctx.debug);
+    case 9: return launch_wg_partials<9>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, ctx.status, ctx.stream, ctx.debug);
+    default: return VKT_ERROR_UNSUPPORTED;
+    }
+}
+
+vktError reduce_weight_grad(const float* partials, size_t nspatial, int k, float* gw, const Ctx& ctx)
+{
+    launch_reduce(partials, nspatial, k, gw, nullptr, ctx.stream);
+    return from_cuda(cudaGetLastError());
 }
 
 }  // namespace vkt
@@ -316,47 +368,27 @@ vktError noalloc_scratch(float** partials, unsigned** status)
     return VKT_NO_ERROR;
 }
 
-// the weight-gradient kernels with a z chunking small enough for the fixed scratch
+// the weight-gradient kernels over the fixed scratch
 template <int K>
 vktError launch_wg_noalloc(const float* x, const float* gy, int nx, int ny, int nz,
-                           float* partials, unsigned* status, float* gw, cudaStream_t stream)
+                           float* partials, unsigned* status, float* gw, cudaStream_t stream,
+                           int debug)
 {
     using namespace vkt;
-    using Geo = Brick<K, TX, TY>;
-    // geometry() adds z chunks only while the grid is under about 8 CTAs per SM, so a
-    // volume with more than one chunk needs fewer than 16 x SMs x k^2 partial sums; only
-    // single-chunk volumes of many column tiles can exceed the scratch
+    // geometry() adds z chunks only while the grid is under about 8 CTAs per SM (two per
+    // SM for small volumes), so a volume with more than one chunk needs fewer than
+    // 16 x SMs x k^2 partial sums; only single-chunk volumes of many column tiles can
+    // exceed the scratch
     const Geometry g = geometry(nx, ny, nz, K);
-    const int nspatial = g.tiles_x * g.tiles_y * g.chunks;
-    if (static_cast<size_t>(nspatial) * K * K * K > VKT_NOALLOC_SCRATCH_FLOATS)
-        return VKT_ERROR_INVALID_VALUE;
-    WgArgs a;
-    a.x = x;
-    a.gy = gy;
-    a.partials = partials;
-    a.nx = nx;
-    a.ny = ny;
-    a.nz = nz;
-    a.tiles_x = g.tiles_x;
-    a.tiles_y = g.tiles_y;
-    a.zchunk = g.zchunk;
-    a.status = status;
-    alignas(64) CUtensorMap map;
-    a.use_tma = encode_tensor_map_3d(&map, FMT_F32, x, nx, ny, nz, Geo::raw_w(FMT_F32), Geo::FH, 1) ? 1 : 0;
-    if (!a.use_tma) memset(&map, 0, sizeof(map));
-    const size_t smem = wgrad_smem_bytes<K>();
-    cudaError_t e = cudaFuncSetAttribute(k_wgrad<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return from_cuda(e);
+    const size_t nspatial = static_cast<size_t>(g.tiles_x) * g.tiles_y * g.chunks;
+    if (nspatial * K * K * K > VKT_NOALLOC_SCRATCH_FLOATS) return VKT_ERROR_INVALID_VALUE;
     // the call's own status word starts at zero in stream order (a memset allocates nothing)
-    e = cudaMemsetAsync(status, 0, sizeof(unsigned), stream);
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return from_cuda(e);
-    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks), NT, smem, stream>>>(map, a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return from_cuda(e);
-    const int kkk = K * K * K;
-    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, nspatial, kkk, gw, status);
-    count_launches(2);
+    vktError err = launch_wg_partials<K>(x, gy, nx, ny, nz, 1, 0, 0, g, partials, status, stream,
+                                         debug);
+    if (err != VKT_NO_ERROR) return err;
+    launch_reduce(partials, nspatial, K, gw, status, stream);
     return from_cuda(cudaGetLastError());
 }
 
@@ -388,12 +420,13 @@ extern "C" vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStr
     const float* x = static_cast<const float*>(src->data);
     const float* gy = static_cast<const float*>(gradDst->data);
     const int nx = src->dims[0], ny = src->dims[1], nz = src->dims[2];
+    const int dbg = pol.debug;
     switch (filter->k) {
-    case 1: return launch_wg_noalloc<1>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
-    case 3: return launch_wg_noalloc<3>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
-    case 5: return launch_wg_noalloc<5>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
-    case 7: return launch_wg_noalloc<7>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
-    case 9: return launch_wg_noalloc<9>(x, gy, nx, ny, nz, partials, status, gradWeights, stream);
+    case 1: return launch_wg_noalloc<1>(x, gy, nx, ny, nz, partials, status, gradWeights, stream, dbg);
+    case 3: return launch_wg_noalloc<3>(x, gy, nx, ny, nz, partials, status, gradWeights, stream, dbg);
+    case 5: return launch_wg_noalloc<5>(x, gy, nx, ny, nz, partials, status, gradWeights, stream, dbg);
+    case 7: return launch_wg_noalloc<7>(x, gy, nx, ny, nz, partials, status, gradWeights, stream, dbg);
+    case 9: return launch_wg_noalloc<9>(x, gy, nx, ny, nz, partials, status, gradWeights, stream, dbg);
     default: return VKT_ERROR_UNSUPPORTED;
     }
 }

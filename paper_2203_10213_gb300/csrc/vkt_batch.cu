@@ -417,8 +417,12 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
         if (pd < ps + vbytes(src[i]) && ps < pd + vbytes(dst[i])) return VKT_ERROR_INVALID_VALUE;
     }
     if (!triples_disjoint(n, dst, src)) return VKT_ERROR_INVALID_VALUE;
+    // one filter over a batch of equal volumes (a training batch): a single direct launch
+    bool handled = false;
+    vktError err = apply_filter_multi(n, dst, src, filters, &handled);
+    if (handled) return err;
     Ctx ctx;
-    vktError err = get_context(&ctx);
+    err = get_context(&ctx);
     if (err != VKT_NO_ERROR) return err;
     vktExecutionPolicy pol;
     vktGetThreadExecutionPolicy(&pol);

@@ -60,6 +60,8 @@ struct DirectArgs {
     int sx0, sx1, sy1;     // forward: voxels with x in [sx0, sx1) and y < sy1 are stored
     int sfmt, dfmt;
     int zchunk;
+    int gzv;               // z chunks per volume: blockIdx.z = volume * gzv + chunk
+    int64_t vs_src, vs_dst;   // voxels from one volume of the batch to the next
     int use_tma;
     int rows;              // no tensor map: stages filled by per-row bulk copies (forward only)
     int withhold_first;    // fault injection: the first plane's TMA load is never issued
@@ -142,7 +144,11 @@ __global__ void __launch_bounds__(NT)
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
     const int x0 = p.ox0 + blockIdx.x * Cfg::TX, y0 = p.oy0 + blockIdx.y * Cfg::TY;
-    const int zc0 = p.oz0 + blockIdx.z * p.zchunk;
+    // volume of the batch and z chunk of this CTA; the volume's own source and destination
+    const int vol = static_cast<int>(blockIdx.z) / p.gzv;
+    const int zc0 = p.oz0 + (static_cast<int>(blockIdx.z) - vol * p.gzv) * p.zchunk;
+    const void* src = static_cast<const unsigned char*>(p.src) + vol * p.vs_src * fmt_bytes(sfmt);
+    void* dst = static_cast<unsigned char*>(p.dst) + vol * p.vs_dst * (ADJ ? 4 : fmt_bytes(dfmt));
     const int zc1 = min(zc0 + p.zchunk, p.oz0 + p.ez);
     if (zc0 >= zc1) return;
     const int pfirst = zc0 - R;
@@ -161,12 +167,12 @@ __global__ void __launch_bounds__(NT)
         for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
             if (s == 0 && p.withhold_first) continue;
             mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1));
+            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        ADJ ? pfirst + s : clampi(pfirst + s, 0, p.nz - 1), vol);
         }
     } else if (rows) {
         for (int s = 0; s < STAGES && s < nplanes; ++s)
-            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], src, vol_bytes, sfmt, p.nx, p.ny,
                                 p.nz, x0, y0, pfirst + s, tid);
         __syncthreads();   // every thread's expect_tx precedes the single arrival
         if (tid == 0)
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(NT)
         if (tma || rows) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
-            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), p.src, sfmt, p.nx,
+            fill_raw_plain<Geo, NT, !ADJ>(const_cast<unsigned char*>(rs), src, sfmt, p.nx,
                                           p.ny, p.nz, x0, y0, pfirst + it, tid);
             __syncthreads();
         }
@@ -247,11 +253,11 @@ __global__ void __launch_bounds__(NT)
         pend = -1;
         if (tma && tid == 0 && it + STAGES < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_3d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1));
+            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
+                        ADJ ? pfirst + it + STAGES : clampi(pfirst + it + STAGES, 0, p.nz - 1), vol);
             ++issued;
         } else if (rows && it + STAGES < nplanes) {
-            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], p.src, vol_bytes, sfmt, p.nx, p.ny,
+            issue_rows<Geo, NT>(raw + s * rawb, &bars[s], src, vol_bytes, sfmt, p.nx, p.ny,
                                 p.nz, x0, y0, pfirst + it + STAGES, tid);
             pend = s;
         }
@@ -316,9 +322,9 @@ __global__ void __launch_bounds__(NT)
                             const unsigned code = comp_code(cs[sl0][i][x], cc[sl0][i][x], p.a0,
                                                             p.a0lo, p.a1, p.a1lo, p.qmax);
                             if (dfmt == FMT_U16)
-                                static_cast<uint16_t*>(p.dst)[idx + x] = static_cast<uint16_t>(code);
+                                static_cast<uint16_t*>(dst)[idx + x] = static_cast<uint16_t>(code);
                             else
-                                static_cast<unsigned char*>(p.dst)[idx + x] = static_cast<unsigned char>(code);
+                                static_cast<unsigned char*>(dst)[idx + x] = static_cast<unsigned char>(code);
                         }
                     }
                 }
@@ -354,11 +360,11 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                 for (int x = 0; x < RX; ++x) row[x] = lane(sl0, i, x);
                 if (ADJ) {
-                    store_row_adjoint<RX>(static_cast<float*>(p.dst), p.nx, p.ny, p.nz, R, oz, oy,
+                    store_row_adjoint<RX>(static_cast<float*>(dst), p.nx, p.ny, p.nz, R, oz, oy,
                                           ox, row);
                 } else if (oy < yend && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
-                    store_row<RX>(p.dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
+                    store_row<RX>(dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
                 }
             }
         }
@@ -465,24 +471,31 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         if (cudaGetDevice(&dev) == cudaSuccess)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const long target = static_cast<long>(sms) * 8;   // ~2 waves of 4 CTAs per SM
-    const long xy = static_cast<long>(gx) * gy;
-    int chunks = static_cast<int>(std::min<long>((target + xy - 1) / xy, std::max(1, a.ez / 8)));
-    chunks = std::max(chunks, 1);
-    a.zchunk = (a.ez + chunks - 1) / chunks;
+    const int nvol = std::max(job.nvol, 1);
+    a.zchunk = zchunk_for(static_cast<long>(gx) * gy * nvol, a.ez, sms);
     const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
+    a.gzv = gz;
+    a.vs_src = job.vs_src;
+    a.vs_dst = job.vs_dst;
+    // one launch takes at most 65535 / gz volumes (the grid's z extent)
+    const int per_launch = std::max(1, 65535 / gz);
 
     alignas(64) CUtensorMap map;
     const int rawx = Geo::raw_w(job.sfmt);
-    a.use_tma = encode_tensor_map_3d(&map, job.sfmt, job.src, job.nx, job.ny, job.nz, rawx,
-                                     Geo::FH, 1)
-                    ? 1
-                    : 0;
+    const int es = fmt_bytes(job.sfmt);
+    auto encode = [&](const void* base, int nv) {
+        return encode_tensor_map(&map, job.sfmt, base, job.nx, job.ny, job.nz, nv, job.vs_src, rawx,
+                                 Geo::FH, 1);
+    };
+    a.use_tma = encode(job.src, std::min(nvol, per_launch)) ? 1 : 0;
     if (!a.use_tma) memset(&map, 0, sizeof(map));
     // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
-    // per row, when the volume starts on a 16-byte boundary (forward only: the adjoint
+    // per row, when every volume starts on a 16-byte boundary (forward only: the adjoint
     // needs the zero extension a tensor map or the plain loads give)
-    a.rows = (!ADJ && !a.use_tma && reinterpret_cast<uintptr_t>(job.src) % 16 == 0) ? 1 : 0;
+    a.rows = (!ADJ && !a.use_tma && reinterpret_cast<uintptr_t>(job.src) % 16 == 0 &&
+              (job.vs_src * es) % 16 == 0)
+                 ? 1
+                 : 0;
 
     const size_t smem = direct_smem_bytes<K, COMP>(job.sfmt, a.rows != 0);
     // the common float32 destinations get kernels with their formats compiled in
@@ -517,9 +530,18 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d withhold=%d\n",
                 ADJ ? "-adjoint" : (COMP ? "-compensated" : ""), K, gx, gy, gz, a.zchunk, smem,
                 a.use_tma, a.rows, a.withhold_first);
-    kern<<<dim3(gx, gy, gz), NT, smem, ctx.stream>>>(map, a, W);
-    count_launches(1);
-    return from_cuda(cudaGetLastError());
+    const DirectArgs a0 = a;
+    for (int v0 = 0; v0 < nvol; v0 += per_launch) {
+        const int nv = std::min(per_launch, nvol - v0);
+        a.src = static_cast<const unsigned char*>(a0.src) + v0 * a0.vs_src * es;
+        a.dst = static_cast<unsigned char*>(a0.dst) + v0 * a0.vs_dst * (ADJ ? 4 : fmt_bytes(job.dfmt));
+        if (v0 > 0 && a.use_tma && !encode(a.src, nv)) return VKT_ERROR_CUDA;
+        kern<<<dim3(gx, gy, gz * nv), NT, smem, ctx.stream>>>(map, a, W);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return VKT_NO_ERROR;
 }
 
 }  // namespace dir

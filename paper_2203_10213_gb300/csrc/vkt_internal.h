@@ -49,6 +49,11 @@ struct Job {
     // read the real neighbours, clamped at the volume's faces.  Otherwise the whole volume.
     int roi = 0;
     int rx0 = 0, ry0 = 0, rz0 = 0, rx1 = 0, ry1 = 0, rz1 = 0;
+    // A batch of nvol volumes with equal dims and formats filtered by one launch (direct
+    // path): volume v's source starts vs_src voxels after src, its destination vs_dst voxels
+    // after dst.
+    int nvol = 1;
+    int64_t vs_src = 0, vs_dst = 0;
 };
 
 // the output region of a job as [x0, x1) x [y0, y1) x [z0, z1)
@@ -61,6 +66,28 @@ inline void job_region(const Job& j, int& x0, int& y0, int& z0, int& x1, int& y1
         x0 = y0 = z0 = 0;
         x1 = j.nx; y1 = j.ny; z1 = j.nz;
     }
+}
+
+// Planes per z chunk for a grid of `tiles` column tiles (over all volumes of a batch, and
+// all kernel planes of the weight gradient) of ez planes each: about 8 CTAs per SM in total,
+// with chunks of at least 8 planes while that still gives at least one CTA per SM; smaller
+// jobs take shorter chunks (down to one plane, read with its halo planes from L2) until
+// there are about two CTAs per SM.
+inline int zchunk_for(long tiles, int ez, int sms)
+{
+    tiles = tiles < 1 ? 1 : tiles;
+    const long target = static_cast<long>(sms) * 8;
+    const long cap8 = ez / 8 < 1 ? 1 : ez / 8;
+    long chunks = (target + tiles - 1) / tiles;
+    if (tiles * cap8 >= sms) {
+        chunks = chunks < cap8 ? chunks : cap8;
+    } else {
+        const long two = (2L * sms + tiles - 1) / tiles;
+        chunks = chunks < ez ? chunks : ez;
+        chunks = chunks < two ? chunks : two;
+    }
+    chunks = chunks < 1 ? 1 : chunks;
+    return static_cast<int>((ez + chunks - 1) / chunks);
 }
 
 struct Ctx {
@@ -76,11 +103,20 @@ vktError launch_direct_comp(const Job& job, const float* w, int k, const Ctx& ct
 // dL/dsrc of the clamped correlation (float32 gy in job.src, gx in job.dst; gx must be
 // zeroed first: face voxels are accumulated atomically).
 vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx);
-// dL/dw: per-CTA FP32 partial sums into `partials` (capacity `cap` floats), then an FP64
-// reduction into gw (k^3 floats).  `partials` is caller-provided scratch.
+// dL/dw summed over nvol volumes of equal dims (volume v of x at x + v vs_x, of gy at
+// gy + v vs_gy): per-CTA FP32 partial sums into `partials` (capacity `cap` floats), then
+// one FP64 reduction over all of them into gw (k^3 floats).  `partials` is caller-provided
+// scratch of weight_grad_scratch_floats(..., nvol) floats.
 vktError launch_weight_grad(const float* x, const float* gy, int nx, int ny, int nz, int k,
-                            float* partials, size_t cap, float* gw, const Ctx& ctx);
-size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k);
+                            float* partials, size_t cap, float* gw, const Ctx& ctx, int nvol = 1,
+                            int64_t vs_x = 0, int64_t vs_gy = 0);
+size_t weight_grad_scratch_floats(int nx, int ny, int nz, int k, int nvol = 1);
+// The partial sums only (no reduction), for volumes that are not evenly spaced: one launch
+// per volume into its own slice, then reduce_weight_grad once over all slices.
+vktError launch_weight_grad_partials(const float* x, const float* gy, int nx, int ny, int nz,
+                                     int k, float* partials, const Ctx& ctx);
+vktError reduce_weight_grad(const float* partials, size_t nspatial, int k, float* gw,
+                            const Ctx& ctx);
 vktError launch_separable(const Job& job, const float* gx, const float* gy, const float* gz,
                           int k, const Ctx& ctx);
 
@@ -96,6 +132,13 @@ bool separable_needs_comp(const vktStructuredVolume_impl* dst, const vktStructur
 bool direct_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
                        const vktFilter_impl* f);
 
+// Volumes whose data lie evenly spaced, `stride` voxels apart (one volume: stride 0).
+bool evenly_spaced(int32_t n, const vktStructuredVolume* v, int64_t* stride);
+// The one-launch form of a batch that shares one filter over equal, evenly spaced volumes
+// (direct path); *handled is false when the batch does not qualify.
+vktError apply_filter_multi(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
+                            vktFilter* filters, bool* handled);
+
 // Helpers provided by the runtime.
 vktError get_context(Ctx* ctx);
 void count_launches(unsigned n);
@@ -104,5 +147,10 @@ vktError from_cuda(cudaError_t e);
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 bool encode_tensor_map_3d(void* map /* CUtensorMap* */, int fmt, const void* base, int nx,
                           int ny, int nz, int boxx, int boxy, int boxz);
+// The same as a 4-D map (x, y, z, volume) of nvol >= 1 volumes of nx x ny x nz voxels,
+// vstride voxels apart (vstride >= nx ny nz and a multiple of 16 bytes; 0 for one volume).
+// nvol == 0 gives the 3-D map of encode_tensor_map_3d.
+bool encode_tensor_map(void* map, int fmt, const void* base, int nx, int ny, int nz, int nvol,
+                       int64_t vstride, int boxx, int boxy, int boxz);
 
 }  // namespace vkt

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "vkt_internal.h"
 
@@ -198,6 +199,24 @@ bool direct_needs_comp(const vktStructuredVolume_impl* dst, const vktStructuredV
     return bound >= 5e-4;
 }
 
+// Volumes b = 0..n-1 whose data lie `stride` voxels apart (data[b] = data[0] + b stride,
+// stride >= the volume's size): one launch can then address them all.  One volume is evenly
+// spaced with stride 0.
+bool evenly_spaced(int32_t n, const vktStructuredVolume* v, int64_t* stride)
+{
+    *stride = 0;
+    if (n <= 1) return true;
+    const int es = fmt_bytes(v[0]->format);
+    const intptr_t d = static_cast<const char*>(v[1]->data) - static_cast<const char*>(v[0]->data);
+    if (d <= 0 || d % es != 0 || static_cast<uint64_t>(d) < volume_bytes(v[0])) return false;
+    for (int32_t b = 2; b < n; ++b)
+        if (static_cast<const char*>(v[b]->data) - static_cast<const char*>(v[0]->data) !=
+            static_cast<intptr_t>(d) * b)
+            return false;
+    *stride = d / es;
+    return true;
+}
+
 void count_launches(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void uncount_launches(unsigned n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
@@ -214,6 +233,12 @@ vktError from_cuda(cudaError_t e)
 
 bool encode_tensor_map_3d(void* map, int fmt, const void* base, int nx, int ny, int nz,
                           int boxx, int boxy, int boxz)
+{
+    return encode_tensor_map(map, fmt, base, nx, ny, nz, 0, 0, boxx, boxy, boxz);
+}
+
+bool encode_tensor_map(void* map, int fmt, const void* base, int nx, int ny, int nz, int nvol,
+                       int64_t vstride, int boxx, int boxy, int boxz)
 {
     {
         std::lock_guard<std::mutex> lock(g_mutex);
@@ -236,14 +261,22 @@ bool encode_tensor_map_3d(void* map, int fmt, const void* base, int nx, int ny, 
     const CUtensorMapDataType dt = fmt == vktDataFormatUint8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
                                    : fmt == vktDataFormatUint16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
                                                                 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
-                          static_cast<cuuint64_t>(nz)};
-    cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * es,
-                             static_cast<cuuint64_t>(nx) * ny * es};
-    cuuint32_t box[3] = {static_cast<cuuint32_t>(boxx), static_cast<cuuint32_t>(boxy),
-                         static_cast<cuuint32_t>(boxz)};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(static_cast<CUtensorMap*>(map), dt, 3, const_cast<void*>(base), dims,
+    // nvol > 0: a 4-D map whose fourth dimension counts nvol volumes vstride voxels apart
+    // (one volume: vstride 0 stands for the volume's own size); nvol == 0: a 3-D map
+    const int rank = nvol > 0 ? 4 : 3;
+    if (rank == 4 && nvol == 1 && vstride == 0) vstride = static_cast<int64_t>(nx) * ny * nz;
+    if (rank == 4 && ((vstride * es) % 16 != 0 || vstride < static_cast<int64_t>(nx) * ny * nz))
+        return false;
+    cuuint64_t dims[4] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
+                          static_cast<cuuint64_t>(nz),
+                          static_cast<cuuint64_t>(nvol > 0 ? nvol : 1)};
+    cuuint64_t strides[3] = {static_cast<cuuint64_t>(nx) * es,
+                             static_cast<cuuint64_t>(nx) * ny * es,
+                             static_cast<cuuint64_t>(vstride) * es};
+    cuuint32_t box[4] = {static_cast<cuuint32_t>(boxx), static_cast<cuuint32_t>(boxy),
+                         static_cast<cuuint32_t>(boxz), 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(static_cast<CUtensorMap*>(map), dt, rank, const_cast<void*>(base), dims,
                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -705,6 +738,79 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
     return err;
 }
 
+// A batch of n triples that share one dense (or direct-forced) filter, with equal dims,
+// formats and value ranges: the direct path takes one launch over all n volumes when
+// sources and destinations are evenly spaced (else one launch per volume), the tensor path
+// one launch per volume; no graph is built, so a filter whose weights change from call to
+// call (a training step) costs no recapture.  Sets *handled when the batch qualifies (and
+// returns the launches' error); otherwise the caller builds its general batch.
+}  // extern "C"
+
+vktError vkt::apply_filter_multi(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
+                                 vktFilter* filters, bool* handled)
+{
+    *handled = false;
+    const vktFilter_impl* f = filters[0];
+    for (int32_t i = 1; i < n; ++i) {
+        if (filters[i] != f) return VKT_NO_ERROR;
+        for (int a = 0; a < 3; ++a)
+            if (src[i]->dims[a] != src[0]->dims[a]) return VKT_NO_ERROR;
+        if (src[i]->format != src[0]->format || dst[i]->format != dst[0]->format ||
+            src[i]->lo != src[0]->lo || src[i]->hi != src[0]->hi || dst[i]->lo != dst[0]->lo ||
+            dst[i]->hi != dst[0]->hi)
+            return VKT_NO_ERROR;
+    }
+    int path = t_policy.path;
+    if (path == VKT_PATH_AUTO) {
+        if (f->separable) return VKT_NO_ERROR;   // the persistent separable batch
+        path = (f->k >= 5 && tensor_available(dst[0], src[0], f) == VKT_NO_ERROR) ? VKT_PATH_TENSOR
+                                                                                  : VKT_PATH_DIRECT;
+    }
+    if (path == VKT_PATH_SEPARABLE) return VKT_NO_ERROR;
+    if (path == VKT_PATH_TENSOR) {
+        const vktError te = tensor_available(dst[0], src[0], f);
+        if (te != VKT_NO_ERROR) {
+            *handled = true;
+            return te;
+        }
+    }
+    int64_t ss = 0, sd = 0;
+    const bool even = evenly_spaced(n, src, &ss) && evenly_spaced(n, dst, &sd);
+    *handled = true;
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+    Job job{};
+    job.nx = src[0]->dims[0];
+    job.ny = src[0]->dims[1];
+    job.nz = src[0]->dims[2];
+    job.sfmt = src[0]->format;
+    job.dfmt = dst[0]->format;
+    double wsum = 0.0;
+    for (int i = 0; i < f->k * f->k * f->k; ++i) wsum += f->w[i];
+    epilogue(dst[0], src[0], wsum, &job);
+    if (path == VKT_PATH_DIRECT) {
+        job.comp = direct_needs_comp(dst[0], src[0], f) ? 1 : 0;
+        if (even) {
+            job.src = src[0]->data;
+            job.dst = dst[0]->data;
+            job.nvol = n;
+            job.vs_src = ss;
+            job.vs_dst = sd;
+            return launch_direct(job, f->w, f->k, ctx);
+        }
+    }
+    for (int32_t i = 0; i < n && err == VKT_NO_ERROR; ++i) {
+        job.src = src[i]->data;
+        job.dst = dst[i]->data;
+        err = path == VKT_PATH_TENSOR ? launch_tensor(job, f->w, f->k, ctx)
+                                      : launch_direct(job, f->w, f->k, ctx);
+    }
+    return err;
+}
+
+extern "C" {
+
 static vktError check_filter_args(vktStructuredVolume dst, vktStructuredVolume src,
                                   vktFilter filter)
 {
@@ -790,6 +896,125 @@ vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeight
         err = launch_weight_grad(static_cast<const float*>(src->data),
                                  static_cast<const float*>(gradDst->data), nx, ny, nz, k, partials,
                                  cap, gradWeights, ctx);
+        e = cudaFreeAsync(partials, ctx.stream);
+        if (err == VKT_NO_ERROR && e != cudaSuccess) err = from_cuda(e);
+    }
+    return err;
+}
+
+// The volumes a batch call writes must not overlap one another, nor any volume it reads.
+static bool writes_disjoint(int32_t n, const vktStructuredVolume* w, const vktStructuredVolume* r1,
+                            const vktStructuredVolume* r2)
+{
+    struct Span {
+        uintptr_t lo, hi;
+    };
+    std::vector<Span> d;
+    d.reserve(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(w[i]->data);
+        d.push_back({lo, lo + volume_bytes(w[i])});
+    }
+    std::sort(d.begin(), d.end(), [](const Span& a, const Span& b) { return a.lo < b.lo; });
+    for (size_t i = 1; i < d.size(); ++i)
+        if (d[i].lo < d[i - 1].hi) return false;
+    for (const vktStructuredVolume* r : {r1, r2}) {
+        for (int32_t j = 0; j < n; ++j) {
+            const uintptr_t lo = reinterpret_cast<uintptr_t>(r[j]->data);
+            const uintptr_t hi = lo + volume_bytes(r[j]);
+            auto it = std::lower_bound(d.begin(), d.end(), hi,
+                                       [](const Span& s, uintptr_t v) { return s.lo < v; });
+            if (it != d.begin() && (it - 1)->hi > lo) return false;
+        }
+    }
+    return true;
+}
+
+vktError vktApplyFilterBackwardBatchSV(int32_t n, vktStructuredVolume* gradSrcs, float* gradWeights,
+                                       vktStructuredVolume* gradDsts, vktStructuredVolume* srcs,
+                                       vktFilter filter)
+{
+    if (n < 1 || !gradDsts || !srcs) return VKT_ERROR_INVALID_VALUE;
+    if (!valid(filter)) return VKT_ERROR_INVALID_HANDLE;
+    for (int32_t b = 0; b < n; ++b) {
+        if (!valid(gradDsts[b]) || !valid(srcs[b])) return VKT_ERROR_INVALID_HANDLE;
+        if (gradSrcs && !valid(gradSrcs[b])) return VKT_ERROR_INVALID_HANDLE;
+        if (srcs[b]->format != vktDataFormatFloat32 || gradDsts[b]->format != vktDataFormatFloat32 ||
+            (gradSrcs && gradSrcs[b]->format != vktDataFormatFloat32))
+            return VKT_ERROR_UNSUPPORTED;
+        for (int a = 0; a < 3; ++a) {
+            if (srcs[b]->dims[a] != srcs[0]->dims[a] || gradDsts[b]->dims[a] != srcs[0]->dims[a])
+                return VKT_ERROR_DIMS_MISMATCH;
+            if (gradSrcs && gradSrcs[b]->dims[a] != srcs[0]->dims[a]) return VKT_ERROR_DIMS_MISMATCH;
+        }
+    }
+    if (gradSrcs && !writes_disjoint(n, gradSrcs, gradDsts, srcs)) return VKT_ERROR_INVALID_VALUE;
+    if (reinterpret_cast<uintptr_t>(gradWeights) % 4 != 0) return VKT_ERROR_INVALID_VALUE;
+    Ctx ctx;
+    vktError err = get_context(&ctx);
+    if (err != VKT_NO_ERROR) return err;
+    const int k = filter->k;
+    const int nx = srcs[0]->dims[0], ny = srcs[0]->dims[1], nz = srcs[0]->dims[2];
+    int64_t s_x = 0, s_gy = 0, s_gx = 0;
+    const bool even_x = evenly_spaced(n, srcs, &s_x);
+    const bool even_gy = evenly_spaced(n, gradDsts, &s_gy);
+    const bool even_gx = gradSrcs && evenly_spaced(n, gradSrcs, &s_gx);
+    if (gradSrcs) {
+        // face voxels of dL/dsrc are accumulated atomically: start from zero
+        const uint64_t vb = volume_bytes(gradSrcs[0]);
+        const bool packed = even_gx && (n == 1 || static_cast<uint64_t>(s_gx) * 4 == vb);
+        for (int32_t b = 0; b < (packed ? 1 : n); ++b) {
+            cudaError_t e = cudaMemsetAsync(gradSrcs[b]->data, 0, packed ? vb * n : vb, ctx.stream);
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        Job job{};
+        job.nx = nx;
+        job.ny = ny;
+        job.nz = nz;
+        job.sfmt = vktDataFormatFloat32;
+        job.dfmt = vktDataFormatFloat32;
+        job.a0 = 0.f;
+        job.a1 = 1.f;
+        job.qmax = 0.f;
+        if (even_gy && even_gx) {
+            // the whole batch in one launch
+            job.src = gradDsts[0]->data;
+            job.dst = gradSrcs[0]->data;
+            job.nvol = n;
+            job.vs_src = s_gy;
+            job.vs_dst = s_gx;
+            err = launch_adjoint(job, filter->w, k, ctx);
+        } else {
+            for (int32_t b = 0; b < n && err == VKT_NO_ERROR; ++b) {
+                job.src = gradDsts[b]->data;
+                job.dst = gradSrcs[b]->data;
+                err = launch_adjoint(job, filter->w, k, ctx);
+            }
+        }
+        if (err != VKT_NO_ERROR) return err;
+    }
+    if (gradWeights) {
+        // every volume's per-CTA partial sums in one stream-ordered scratch, reduced together
+        const bool one = even_x && even_gy;
+        const size_t per = weight_grad_scratch_floats(nx, ny, nz, k, 1);
+        const size_t cap = one ? weight_grad_scratch_floats(nx, ny, nz, k, n) : per * n;
+        float* partials = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&partials), cap * sizeof(float),
+                                        ctx.stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        if (one) {
+            err = launch_weight_grad(static_cast<const float*>(srcs[0]->data),
+                                     static_cast<const float*>(gradDsts[0]->data), nx, ny, nz, k,
+                                     partials, cap, gradWeights, ctx, n, s_x, s_gy);
+        } else {
+            for (int32_t b = 0; b < n && err == VKT_NO_ERROR; ++b)
+                err = launch_weight_grad_partials(static_cast<const float*>(srcs[b]->data),
+                                                  static_cast<const float*>(gradDsts[b]->data), nx,
+                                                  ny, nz, k, partials + per * b, ctx);
+            if (err == VKT_NO_ERROR)
+                err = reduce_weight_grad(partials, per * n / (static_cast<size_t>(k) * k * k), k,
+                                         gradWeights, ctx);
+        }
         e = cudaFreeAsync(partials, ctx.stream);
         if (err == VKT_NO_ERROR && e != cudaSuccess) err = from_cuda(e);
     }

@@ -590,14 +590,15 @@ def small_form(vkt, torch, stream, lib, dev):
 def differentiation_form(vkt, torch, stream, lib, dev):
     """One training step's filter work on a batch of 8 float32 blob volumes of 128^3 with a
     learnable dense 5^3 kernel (N(0, 0.1)), the loss being the mean squared difference to
-    the same volumes filtered by a hidden 5^3 kernel: the forward filter of each volume
-    (dense direct path), then vktApplyFilterBackwardSV per volume (dL/dx by the exact
-    adjoint, dL/dw by the per-tap reduction with FP64 cross-block sums).  The loss gradient
-    dL/dy = 2 (y - y*) / N is formed between the two by torch (the caller's loss, not the
-    filter) and is not timed.  Reports forward and backward ms per batch, forward+backward
-    Gvoxel/s (output voxels of the forward), and the fraction of the FP32 FMA peak
-    (SMs x 128 FMA per clock x the maximum SM clock) on the algorithmic 3 x 125 FMA per
-    voxel."""
+    the same volumes filtered by a hidden 5^3 kernel: the forward filter of the batch
+    (vktApplyFilterBatchSV with one filter: one direct launch over the 8 volumes), then
+    vktApplyFilterBackwardBatchSV (dL/dx by the exact adjoint in one launch, dL/dw by the
+    per-tap reduction in one launch plus one FP64 reduction over the whole batch).  The loss
+    gradient dL/dy = 2 (y - y*) / N is formed between the two by torch (the caller's loss, not
+    the filter) and is not timed.  Reports forward and backward ms per batch, the library's
+    launches per step, forward+backward Gvoxel/s (output voxels of the forward), and the
+    fraction of the FP32 FMA peak (SMs x 128 FMA per clock x the maximum SM clock) on the
+    algorithmic 3 x 125 FMA per voxel."""
     import ctypes
     import synth
     B, n, k = 8, 128, 5
@@ -608,7 +609,7 @@ def differentiation_form(vkt, torch, stream, lib, dev):
     f, fh = vkt.Filter.dense(w0), vkt.Filter.dense(wh)
     y, target, gy = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
     gx = torch.zeros_like(x)
-    gw = torch.zeros((B, k ** 3), dtype=torch.float32, device=dev)
+    gw = torch.zeros(k ** 3, dtype=torch.float32, device=dev)
     vx = [vkt.StructuredVolume.from_tensor(x[b]) for b in range(B)]
     vy = [vkt.StructuredVolume.from_tensor(y[b]) for b in range(B)]
     vt = [vkt.StructuredVolume.from_tensor(target[b]) for b in range(B)]
@@ -616,24 +617,27 @@ def differentiation_form(vkt, torch, stream, lib, dev):
     vgy = [vkt.StructuredVolume.from_tensor(gy[b]) for b in range(B)]
     reps = 10
     fwd_ms, bwd_ms = [], []
+    arr = ctypes.c_void_p * B
+    h_x, h_y, h_t = (arr(*(v.handle.value for v in vs)) for vs in (vx, vy, vt))
+    h_gx, h_gy = (arr(*(v.handle.value for v in vs)) for vs in (vgx, vgy))
+    h_f, h_fh = arr(*([f.handle.value] * B)), arr(*([fh.handle.value] * B))
+    launches = 0
     with vkt.policy(stream=stream, path="direct"):
-        for b in range(B):
-            vkt.check(lib.vktApplyFilterSV(vt[b].handle, vx[b].handle, fh.handle))
+        vkt.check(lib.vktApplyFilterBatchSV(B, h_t, h_x, h_fh))
         for it in range(3 + reps):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            l0 = vkt.launch_count()
             ev[0].record(stream)
-            for b in range(B):
-                vkt.check(lib.vktApplyFilterSV(vy[b].handle, vx[b].handle, f.handle))
+            vkt.check(lib.vktApplyFilterBatchSV(B, h_y, h_x, h_f))
             ev[1].record(stream)
             with torch.cuda.stream(stream):
                 torch.sub(y, target, out=gy)
                 gy.mul_(2.0 / y.numel())
             ev[2].record(stream)
-            for b in range(B):
-                vkt.check(lib.vktApplyFilterBackwardSV(
-                    vgx[b].handle, ctypes.c_void_p(gw[b].data_ptr()), vgy[b].handle,
-                    vx[b].handle, f.handle))
+            vkt.check(lib.vktApplyFilterBackwardBatchSV(B, h_gx, ctypes.c_void_p(gw.data_ptr()), h_gy,
+                                                        h_x, f.handle))
             ev[3].record(stream)
+            launches = vkt.launch_count() - l0
             torch.cuda.synchronize()
             vkt.synchronize()
             if it >= 3:
@@ -651,7 +655,9 @@ def differentiation_form(vkt, torch, stream, lib, dev):
         h.destroy()
     f.destroy()
     fh.destroy()
-    return {"batch": B, "dims": [n, n, n], "k": k, "path": "direct (forward), adjoint + weight reduction (backward)",
+    return {"batch": B, "dims": [n, n, n], "k": k,
+            "path": "direct over the batch (forward), adjoint + weight reduction over the batch (backward)",
+            "library_launches_per_step": launches,
             "forward_ms": round(fms, 4), "backward_ms": round(bms, 4),
             "forward_gvoxel_s": round(vox / (fms * 1e-3) / 1e9, 2),
             "fwd_bwd_gvoxel_s": round(vox / ((fms + bms) * 1e-3) / 1e9, 2),

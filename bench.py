@@ -355,6 +355,7 @@ def batching_form(args, vkt, torch, dev, stream):
         vkt.synchronize()
         return a.elapsed_time(b) / reps
 
+    import ctypes
     with vkt.policy(stream=stream):
         def batched():
             vkt.apply_filter_batch(vd, vs, fs, stream=stream)
@@ -363,7 +364,15 @@ def batching_form(args, vkt, torch, dev, stream):
             for i in range(len(items)):
                 vkt.check(lib.vktApplyFilterSV(vd[i].handle, vs[i].handle, fs[i].handle))
 
+        # the fixed rule (64-plane bricks, full occupancy), then the autotuned plan (its first
+        # call, untimed, measures the candidates)
+        enabled = ctypes.c_int32()
+        vkt.check(lib.vktAutotuneGetEnabled(ctypes.byref(enabled)))
+        vkt.check(lib.vktAutotuneSetEnabled(0))
+        ms_rule = timed(batched)
+        vkt.check(lib.vktAutotuneSetEnabled(1))
         ms_batch = timed(batched)
+        vkt.check(lib.vktAutotuneSetEnabled(enabled.value))
         ms_sep = timed(separate)
         # sum of individually timed launches
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -379,6 +388,8 @@ def batching_form(args, vkt, torch, dev, stream):
             "graph_batch_ms": round(ms_batch, 4),
             "graph_batch_gvoxel_s": round(vox / (ms_batch * 1e-3) / 1e9, 2),
             "graph_batch_frac_hbm": round(nbytes / (ms_batch * 1e-3) / 1e9 / hbm, 4),
+            "graph_batch_fixed_rule_ms": round(ms_rule, 4),
+            "tuned_over_fixed_rule": round(ms_rule / ms_batch, 3),
             "separate_back_to_back_ms": round(ms_sep, 4),
             "separate_sum_of_launches_ms": round(ms_sum, 4),
             "speedup_vs_back_to_back": round(ms_sep / ms_batch, 3),

@@ -101,6 +101,36 @@ typedef struct vktExecutionPolicy {
 VKT_API vktError vktSetThreadExecutionPolicy(vktExecutionPolicy policy);
 VKT_API vktError vktGetThreadExecutionPolicy(vktExecutionPolicy* policy);
 
+/*
+ * Autotuner.  Under VKT_PATH_AUTO the library picks the evaluation path and the launch shape
+ * of each call (Sec. 3.2 allows a specialised implementation of an algorithm as long as its
+ * behaviour stays the same; every choice here computes the same result within the method's
+ * tolerance, and the brick shapes the same bits).  Without the autotuner the choice is a
+ * fixed rule: separable filters take the separable path, dense k >= 5 filters on float32
+ * volumes the tensor cores, the rest the direct path, with the launchers' brick z extents.
+ * With it (the default; VKT_AUTOTUNE=0 in the environment starts the process with it off),
+ * the first call of each call shape -- filter size and kind, formats, region or whole volume,
+ * extent rounded up to powers of two per axis -- times its candidates on the policy stream
+ * (the rule's path, for dense filters that the tensor path can evaluate also the other
+ * path, and three brick z extents of the CUDA-core paths), keeps the fastest and uses it
+ * from then on.  That first call synchronises the policy stream and launches each candidate
+ * three times into the destination (the last launch is the chosen one); a call made while
+ * its stream is being captured into a graph uses the rule.  vktApplyFilterBatchSV tunes
+ * each new batch plan the same way (brick z extent, persistent grid).  The choices live in
+ * memory; when VKT_AUTOTUNE_CACHE names a file they are read from it at the first lookup and
+ * written back after every new choice (JSON, see vktAutotuneSave).
+ */
+VKT_API vktError vktAutotuneSetEnabled(int32_t enabled);
+VKT_API vktError vktAutotuneGetEnabled(int32_t* enabled);
+/* Forgets every choice held in memory (a VKT_AUTOTUNE_CACHE file is not reread). */
+VKT_API vktError vktAutotuneClear(void);
+VKT_API vktError vktAutotuneGetCount(int32_t* count);
+/* Writes the choices to `path` as {"vkt_autotune": 1, "entries": [{"key": K, "path": P,
+ * "zchunk": Z, "ms": T}, ...]}, one entry per line; INVALID_VALUE if it cannot be written. */
+VKT_API vktError vktAutotuneSave(const char* path);
+/* Adds the entries of a file written by vktAutotuneSave; INVALID_VALUE if it cannot be read. */
+VKT_API vktError vktAutotuneLoad(const char* path);
+
 /* Short English description of an error code; never NULL. */
 VKT_API const char* vktGetErrorString(vktError error);
 

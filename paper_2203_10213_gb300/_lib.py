@@ -66,6 +66,12 @@ SIGNATURES = {
     "vktApplyFilterBackwardSV": [p, p, p, p, p],
     "vktApplyFilterBackwardBatchSV": [i32, ctypes.POINTER(p), p, ctypes.POINTER(p), ctypes.POINTER(p), p],
     "vktApplyFilterWeightGradNoAllocSV": [p, p, p, p],
+    "vktAutotuneSetEnabled": [i32],
+    "vktAutotuneGetEnabled": [pi32],
+    "vktAutotuneClear": [],
+    "vktAutotuneGetCount": [pi32],
+    "vktAutotuneSave": [ctypes.c_char_p],
+    "vktAutotuneLoad": [ctypes.c_char_p],
 }
 
 

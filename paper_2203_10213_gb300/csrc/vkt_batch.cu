@@ -205,19 +205,23 @@ void epilogue_of(const vktStructuredVolume_impl* dst, const vktStructuredVolume_
     }
 }
 
-int batch_zchunk(int nz)
+// Planes per brick along z for a volume of nz planes: whole volumes up to 1.5 x `target`
+// planes, else equal chunks of about `target` planes.
+int batch_zchunk(int nz, int target)
 {
-    if (nz <= 96) return nz;
-    const int chunks = (nz + 63) / 64;
+    if (2 * nz <= 3 * target) return nz;
+    const int chunks = (nz + target - 1) / target;
     return (nz + chunks - 1) / chunks;
 }
 
 // sep_idx: triples for the persistent kernel; dense_idx: triples launched on their own
 // (dense filters, and separable ones of k = 9) inside the same graph.
+// zt: brick z extent target (batch_zchunk); per_sm_cap: CTAs per SM of the persistent grids
+// (0: as many as the occupancy allows)
 vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
                     vktFilter* filters, const std::vector<int>& sep_idx,
                     const std::vector<int>& dense_idx, bool force_dense, bool force_direct,
-                    const Ctx& ctx)
+                    const Ctx& ctx, int zt = 64, int per_sm_cap = 0)
 {
     // work list: separable volumes' bricks, heavy kernels first
     std::vector<int4> items;
@@ -241,7 +245,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         J.k = filters[i]->k;
         J.comp = separable_needs_comp(dst[i], s, filters[i]) ? 1 : 0;
         const int ty = J.comp ? sep::CTY : sep::TY;
-        J.zchunk = batch_zchunk(J.nz);
+        J.zchunk = batch_zchunk(J.nz, zt);
         J.tiles_x = (J.nx + sep::TX - 1) / sep::TX;
         J.tiles_y = (J.ny + ty - 1) / ty;
         J.chunks = (J.nz + J.zchunk - 1) / J.zchunk;
@@ -304,6 +308,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         if (e != cudaSuccess) return from_cuda(e);
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<false>, sep::NT, smem_fast);
+        if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
         grid_fast = static_cast<int>(std::min<long>(nfast, static_cast<long>(sms) * std::max(per_sm, 1)));
     }
     if (ncomp > 0) {
@@ -312,6 +317,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         if (e != cudaSuccess) return from_cuda(e);
         int per_sm = 1;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<true>, sep::NT, smem_comp);
+        if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
         grid_comp = static_cast<int>(std::min<long>(ncomp, static_cast<long>(sms) * std::max(per_sm, 1)));
     }
 
@@ -393,8 +399,8 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     P.kernels = kernels;
     if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] batch plan: %zu separable volumes, %d + %d compensated bricks, "
-                "grids %d / %d, %zu single launches\n", P.jobs.size(), nfast, ncomp, grid_fast,
-                grid_comp, dense_idx.size());
+                "grids %d / %d, %zu single launches, brick z target %d, CTAs per SM cap %d\n",
+                P.jobs.size(), nfast, ncomp, grid_fast, grid_comp, dense_idx.size(), zt, per_sm_cap);
     return VKT_NO_ERROR;
 }
 
@@ -431,9 +437,16 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
 
     std::vector<int> sep_idx, dense_idx;
     std::vector<unsigned char> key;
+    // the autotuner's key of the batch: its shape without the data pointers (FNV-1a hash)
+    uint64_t shape_hash = 1469598103934665603ull;
+    auto mix = [&](const void* v, size_t b) {
+        const unsigned char* q = static_cast<const unsigned char*>(v);
+        for (size_t t = 0; t < b; ++t) shape_hash = (shape_hash ^ q[t]) * 1099511628211ull;
+    };
     put(key, dev);
     put(key, n);
     put(key, pol.path);
+    put(key, autotune_enabled());
     for (int i = 0; i < n; ++i) {
         const bool s = filters[i]->separable && filters[i]->k <= 7 && pol.path != VKT_PATH_DIRECT &&
                        pol.path != VKT_PATH_TENSOR;
@@ -446,6 +459,10 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
         put(key, dst[i]->format);
         put(key, filters[i]->k);
         put(key, s && separable_needs_comp(dst[i], src[i], filters[i]));
+        const int shape[7] = {s ? 1 : 0, src[i]->dims[0], src[i]->dims[1], src[i]->dims[2],
+                              static_cast<int>(src[i]->format) * 4 + static_cast<int>(dst[i]->format),
+                              filters[i]->k, s && separable_needs_comp(dst[i], src[i], filters[i])};
+        mix(shape, sizeof(shape));
         if (!s) {
             // dense launches bake weights and ranges into the graph
             key.insert(key.end(), reinterpret_cast<const unsigned char*>(filters[i]->w),
@@ -477,15 +494,60 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
     std::lock_guard<std::mutex> lock(g_plans_mutex);
     auto it = std::find_if(g_plans.begin(), g_plans.end(), [&](const Plan& p) { return p.key == key; });
     if (it == g_plans.end()) {
+        const bool force_dense = pol.path == VKT_PATH_DIRECT || pol.path == VKT_PATH_TENSOR;
+        const bool force_direct = pol.path == VKT_PATH_DIRECT;
+        cudaStream_t pstream = static_cast<cudaStream_t>(pol.stream);
+        // brick z extent and persistent grid: the tuned choice of this batch shape, else the
+        // rule (64-plane bricks, as many CTAs per SM as fit), else measured now
+        char tkey[96];
+        std::snprintf(tkey, sizeof(tkey), "batch n%d %016llx", n,
+                      static_cast<unsigned long long>(shape_hash));
+        TuneChoice tc;
+        tc.zchunk = 64;
+        tc.path = 0;
+        const bool tune = !sep_idx.empty() && autotune_enabled() && pol.path == VKT_PATH_AUTO;
+        bool measure = false;
+        if (tune && !autotune_lookup(tkey, &tc)) measure = !stream_capturing(pstream);
         Plan P;
-        P.key = key;
-        P.device = dev;
-        err = build_plan(P, n, dst, src, filters, sep_idx, dense_idx,
-                         pol.path == VKT_PATH_DIRECT || pol.path == VKT_PATH_TENSOR,
-                         pol.path == VKT_PATH_DIRECT, ctx);
-        if (err != VKT_NO_ERROR) {
-            P.release();
-            return err;
+        if (measure) {
+            // every candidate plan is built and replayed on the policy stream; the fastest
+            // is kept (the replays write the destinations, as the call itself does)
+            const TuneChoice cand[5] = {{0, 64, 0.f}, {0, 32, 0.f}, {0, 128, 0.f}, {1, 64, 0.f},
+                                        {1, 32, 0.f}};
+            std::vector<Plan> plans(5);
+            for (int c = 0; c < 5 && err == VKT_NO_ERROR; ++c) {
+                plans[c].key = key;
+                plans[c].device = dev;
+                err = build_plan(plans[c], n, dst, src, filters, sep_idx, dense_idx, force_dense,
+                                 force_direct, ctx, cand[c].zchunk, cand[c].path);
+            }
+            if (err == VKT_NO_ERROR) {
+                err = autotune_time(cand, 5, [&](const TuneChoice& t) {
+                    const int c = static_cast<int>(&t - cand);
+                    count_launches(plans[c].kernels);
+                    return from_cuda(cudaGraphLaunch(plans[c].exec, pstream));
+                }, pstream, &tc);
+            }
+            int keep = -1;
+            for (int c = 0; c < 5; ++c)
+                if (err == VKT_NO_ERROR && cand[c].zchunk == tc.zchunk && cand[c].path == tc.path) keep = c;
+            for (int c = 0; c < 5; ++c)
+                if (c != keep) plans[c].release();
+            if (err != VKT_NO_ERROR || keep < 0) return err != VKT_NO_ERROR ? err : VKT_ERROR_CUDA;
+            autotune_store(tkey, tc);
+            if (ctx.debug & VKT_DEBUG_LOG)
+                fprintf(stderr, "[vkt] autotune %s: brick z target %d, CTAs per SM cap %d, %.4f ms\n",
+                        tkey, tc.zchunk, tc.path, tc.ms);
+            P = std::move(plans[keep]);
+        } else {
+            P.key = key;
+            P.device = dev;
+            err = build_plan(P, n, dst, src, filters, sep_idx, dense_idx, force_dense, force_direct,
+                             ctx, tc.zchunk > 0 ? tc.zchunk : 64, std::max(0, tc.path));
+            if (err != VKT_NO_ERROR) {
+                P.release();
+                return err;
+            }
         }
         g_plans.push_front(std::move(P));
         while (g_plans.size() > MAX_PLANS) {

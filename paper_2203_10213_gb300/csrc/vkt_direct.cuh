@@ -472,7 +472,8 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int nvol = std::max(job.nvol, 1);
-    a.zchunk = zchunk_for(static_cast<long>(gx) * gy * nvol, a.ez, sms);
+    a.zchunk = job.zchunk > 0 ? std::min(job.zchunk, a.ez)
+                              : zchunk_for(static_cast<long>(gx) * gy * nvol, a.ez, sms);
     const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
     a.gzv = gz;
     a.vs_src = job.vs_src;

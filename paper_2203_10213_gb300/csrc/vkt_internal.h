@@ -54,6 +54,9 @@ struct Job {
     // after dst.
     int nvol = 1;
     int64_t vs_src = 0, vs_dst = 0;
+    // Planes per z chunk of a brick (direct and separable paths); 0: the launcher's rule.
+    // The chunking changes no result, only the launch shape (the autotuner sets it).
+    int zchunk = 0;
 };
 
 // the output region of a job as [x0, x1) x [y0, y1) x [z0, z1)
@@ -152,5 +155,58 @@ bool encode_tensor_map_3d(void* map /* CUtensorMap* */, int fmt, const void* bas
 // nvol == 0 gives the 3-D map of encode_tensor_map_3d.
 bool encode_tensor_map(void* map, int fmt, const void* base, int nx, int ny, int nz, int nvol,
                        int64_t vstride, int boxx, int boxy, int boxz);
+
+// Autotuner (vkt_tune.cu).  A choice for one call shape: the evaluation path and the z
+// chunk of the CUDA-core paths (0: the rule), or for a batch its brick z extent and its
+// persistent grid's CTAs per SM (0: as many as fit).
+struct TuneChoice {
+    int path = 0;
+    int zchunk = 0;
+    float ms = 0.f;
+};
+bool autotune_enabled();
+bool autotune_lookup(const char* key, TuneChoice* c);
+void autotune_store(const char* key, const TuneChoice& c);
+// Whether work enqueued on `stream` now would be captured into a graph (no timing then).
+bool stream_capturing(cudaStream_t stream);
+// Times run(candidate) for every candidate on `stream` (one untimed launch, then two timed
+// with CUDA events; candidates whose launch fails are skipped) and returns the fastest in
+// *best (VKT_ERROR_UNSUPPORTED when none ran).  Synchronises the stream.
+template <class Run>
+vktError autotune_time(const TuneChoice* cand, int n, Run run, cudaStream_t stream, TuneChoice* best)
+{
+    cudaEvent_t ev[2];
+    if (cudaEventCreate(&ev[0]) != cudaSuccess) return from_cuda(cudaGetLastError());
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return from_cuda(cudaGetLastError());
+    }
+    bool found = false;
+    vktError err = VKT_NO_ERROR;
+    for (int i = 0; i < n; ++i) {
+        if (run(cand[i]) != VKT_NO_ERROR) continue;
+        cudaEventRecord(ev[0], stream);
+        vktError e1 = run(cand[i]);
+        vktError e2 = e1 == VKT_NO_ERROR ? run(cand[i]) : e1;
+        cudaEventRecord(ev[1], stream);
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+            err = from_cuda(cudaGetLastError());
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e2 != VKT_NO_ERROR) continue;
+        ms *= 0.5f;
+        if (!found || ms < best->ms) {
+            *best = cand[i];
+            best->ms = ms;
+            found = true;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (err != VKT_NO_ERROR) return err;
+    return found ? VKT_NO_ERROR : VKT_ERROR_UNSUPPORTED;
+}
 
 }  // namespace vkt

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "vkt_internal.h"
@@ -657,8 +658,41 @@ vktError vktFilterDestroy(vktFilter f)
 
 // ------------------------------------------------------------------ ApplyFilter
 
+// The autotuner's key of a single-volume call: filter size and kind, formats, the
+// compensated mode, region or whole volume, and the extent filtered, each axis rounded up to
+// a power of two (a size class), plus the SM count of the device.
+static std::string tune_key(const vktStructuredVolume_impl* dst, const vktStructuredVolume_impl* src,
+                            const vktFilter_impl* f, const int32_t* ext, bool roi, bool tensor_ok)
+{
+    auto cls = [](int v) {
+        int c = 1;
+        while (c < v) c <<= 1;
+        return c;
+    };
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "filter k%d %s s%d d%d %s %dx%dx%d sm%d", f->k,
+                  f->separable ? "separable" : (tensor_ok ? "dense-tc" : "dense"),
+                  static_cast<int>(src->format),
+                  static_cast<int>(dst->format), roi ? "range" : "volume", cls(ext[0]), cls(ext[1]),
+                  cls(ext[2]), sms);
+    return buf;
+}
+
 // ApplyFilter on the whole volume (box == nullptr) or on the region
-// [box[0], box[3]) x [box[1], box[4]) x [box[2], box[5]) (validated by the caller)
+// [box[0], box[3]) x [box[1], box[4]) x [box[2], box[5]) (validated by the caller).
+//
+// Path and launch shape: a forced policy path is used as given, with the launchers' rules.
+// Under VKT_PATH_AUTO the fixed rule is separable for separable filters, tensor cores for
+// dense k >= 5 float32 volumes that a tensor map describes (whole volumes), else direct;
+// with the autotuner enabled, the first call of each call shape (tune_key) instead times
+// the candidates -- the rule's path and, for dense filters the tensor path could also
+// evaluate, the other one; for the CUDA-core paths three brick z extents (the rule's, and
+// about 16 and 4 chunks per volume) -- on the policy stream and keeps the fastest.  A
+// separable filter keeps its separable path (the batch computes the same bits).  No timing
+// happens while the stream is being captured into a graph: the rule is used instead.
 static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter,
                              const int32_t* box)
 {
@@ -667,11 +701,13 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
     if (err != VKT_NO_ERROR) return err;
 
     const int k = filter->k;
+    const bool auto_path = t_policy.path == VKT_PATH_AUTO;
     int path = t_policy.path;
-    if (path == VKT_PATH_AUTO) {
+    const bool tensor_ok = !box && k >= 5 && tensor_available(dst, src, filter) == VKT_NO_ERROR;
+    if (auto_path) {
         if (filter->separable)
             path = VKT_PATH_SEPARABLE;
-        else if (!box && k >= 5 && tensor_available(dst, src, filter) == VKT_NO_ERROR)
+        else if (tensor_ok)
             path = VKT_PATH_TENSOR;
         else
             path = VKT_PATH_DIRECT;
@@ -683,35 +719,90 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
         if (err != VKT_NO_ERROR) return err;
     }
 
-    Job job{};
+    Job base{};
     if (box) {
-        job.roi = 1;
-        job.rx0 = box[0];
-        job.ry0 = box[1];
-        job.rz0 = box[2];
-        job.rx1 = box[3];
-        job.ry1 = box[4];
-        job.rz1 = box[5];
+        base.roi = 1;
+        base.rx0 = box[0];
+        base.ry0 = box[1];
+        base.rz0 = box[2];
+        base.rx1 = box[3];
+        base.ry1 = box[4];
+        base.rz1 = box[5];
     }
-    job.src = src->data;
-    job.dst = dst->data;
-    job.nx = src->dims[0];
-    job.ny = src->dims[1];
-    job.nz = src->dims[2];
-    job.sfmt = src->format;
-    job.dfmt = dst->format;
-    double wsum = 0.0;
-    if (path == VKT_PATH_SEPARABLE) {
-        double s[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < 3; ++a)
-            for (int i = 0; i < k; ++i) s[a] += filter->g[a][i];
-        wsum = s[0] * s[1] * s[2];
-    } else {
-        for (int i = 0; i < k * k * k; ++i) wsum += filter->w[i];
+    base.src = src->data;
+    base.dst = dst->data;
+    base.nx = src->dims[0];
+    base.ny = src->dims[1];
+    base.nz = src->dims[2];
+    base.sfmt = src->format;
+    base.dfmt = dst->format;
+    // the job of one path: epilogue constants from that path's weight sum, compensated mode
+    auto job_for = [&](int p, int zchunk) {
+        Job job = base;
+        double wsum = 0.0;
+        if (p == VKT_PATH_SEPARABLE) {
+            double sv[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < 3; ++a)
+                for (int i = 0; i < k; ++i) sv[a] += filter->g[a][i];
+            wsum = sv[0] * sv[1] * sv[2];
+        } else {
+            for (int i = 0; i < k * k * k; ++i) wsum += filter->w[i];
+        }
+        epilogue(dst, src, wsum, &job);
+        if (p == VKT_PATH_SEPARABLE) job.comp = separable_needs_comp(dst, src, filter) ? 1 : 0;
+        if (p == VKT_PATH_DIRECT) job.comp = direct_needs_comp(dst, src, filter) ? 1 : 0;
+        job.zchunk = zchunk;
+        return job;
+    };
+    auto launch = [&](int p, int zchunk) {
+        const Job job = job_for(p, zchunk);
+        if (p == VKT_PATH_SEPARABLE)
+            return launch_separable(job, filter->g[0], filter->g[1], filter->g[2], k, ctx);
+        if (p == VKT_PATH_TENSOR) return launch_tensor(job, filter->w, k, ctx);
+        return launch_direct(job, filter->w, k, ctx);
+    };
+
+    int zchunk = 0;
+    if (auto_path && autotune_enabled()) {
+        const int32_t ext[3] = {box ? box[3] - box[0] : base.nx, box ? box[4] - box[1] : base.ny,
+                                box ? box[5] - box[2] : base.nz};
+        const std::string key = tune_key(dst, src, filter, ext, box != nullptr, tensor_ok);
+        TuneChoice c;
+        if (autotune_lookup(key.c_str(), &c)) {
+            // a choice read from a file is used only where it can evaluate this call
+            const bool usable = (c.path == VKT_PATH_SEPARABLE && filter->separable) ||
+                                (c.path == VKT_PATH_TENSOR && tensor_ok) ||
+                                c.path == VKT_PATH_DIRECT;
+            if (usable) {
+                path = c.path;
+                zchunk = std::max(0, c.zchunk);
+            }
+        } else if (!stream_capturing(ctx.stream)) {
+            TuneChoice cand[8];
+            int n = 0;
+            const int ez = ext[2];
+            const int zs[3] = {0, std::max(1, (ez + 15) / 16), std::max(1, (ez + 3) / 4)};
+            const int cpath = filter->separable ? VKT_PATH_SEPARABLE : VKT_PATH_DIRECT;
+            for (int i = 0; i < 3; ++i) {
+                if (i > 0 && zs[i] == zs[i - 1]) continue;
+                cand[n].path = cpath;
+                cand[n++].zchunk = zs[i];
+            }
+            if (!filter->separable && tensor_ok) {
+                cand[n].path = VKT_PATH_TENSOR;
+                cand[n++].zchunk = 0;
+            }
+            err = autotune_time(cand, n, [&](const TuneChoice& t) { return launch(t.path, t.zchunk); },
+                                ctx.stream, &c);
+            if (err != VKT_NO_ERROR) return err;
+            autotune_store(key.c_str(), c);
+            if (ctx.debug & VKT_DEBUG_LOG)
+                fprintf(stderr, "[vkt] autotune %s: %d candidates, path=%d zchunk=%d %.4f ms\n",
+                        key.c_str(), n, c.path, c.zchunk, c.ms);
+            path = c.path;
+            zchunk = c.zchunk;
+        }
     }
-    epilogue(dst, src, wsum, &job);
-    if (path == VKT_PATH_SEPARABLE) job.comp = separable_needs_comp(dst, src, filter) ? 1 : 0;
-    if (path == VKT_PATH_DIRECT) job.comp = direct_needs_comp(dst, src, filter) ? 1 : 0;
 
     cudaEvent_t ev[2] = {nullptr, nullptr};
     if (t_policy.printTimes) {
@@ -719,19 +810,14 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
         cudaEventCreate(&ev[1]);
         cudaEventRecord(ev[0], ctx.stream);
     }
-    if (path == VKT_PATH_SEPARABLE)
-        err = launch_separable(job, filter->g[0], filter->g[1], filter->g[2], k, ctx);
-    else if (path == VKT_PATH_TENSOR)
-        err = launch_tensor(job, filter->w, k, ctx);
-    else
-        err = launch_direct(job, filter->w, k, ctx);
+    err = launch(path, zchunk);
     if (t_policy.printTimes) {
         cudaEventRecord(ev[1], ctx.stream);
         cudaEventSynchronize(ev[1]);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         fprintf(stderr, "[vkt] ApplyFilter%s %dx%dx%d k=%d path=%d: %.3f ms\n",
-                box ? "Range" : "", job.nx, job.ny, job.nz, k, path, ms);
+                box ? "Range" : "", base.nx, base.ny, base.nz, k, path, ms);
         cudaEventDestroy(ev[0]);
         cudaEventDestroy(ev[1]);
     }

@@ -65,6 +65,7 @@ KERNEL_CASES = {
     "lap3_ct640": ("blobs", 0, (640, 512, 512), "laplacian3", "direct"),
     "tc7_dns512": ("uniform", 2, (512, 512, 256), "random7", "tensor"),
     "direct7_dns512": ("uniform", 2, (512, 512, 256), "random7", "direct"),
+    "batch256": None,    # the batching form's 256 volumes (run_batch_case)
 }
 
 # Per-launch DRAM traffic of the kernels this bench reports, from the ncu captures summarised
@@ -918,10 +919,41 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batch_case(args):
+    """The 256-volume batch of the batching form, --reps graph launches (fixed rule, no
+    tuning), for profiler captures of the persistent batch kernels."""
+    import ctypes
+    import torch
+    import synth
+    import paper_2203_10213_gb300 as vkt
+    items = synth.batch_recipe(synth.BASE_SEED + 3, n=256)
+    dt = {synth.U8: torch.uint8, synth.U16: torch.uint16, synth.F32: torch.float32}
+    keep, vs, vd, fs = [], [], [], []
+    for it in items:
+        a = synth.volume(it["kind"], it["fmt"], it["dims"], it["seed"])
+        s = torch.from_numpy(a).cuda()
+        d = torch.empty(a.shape, dtype=dt[it["fmt"]], device="cuda")
+        keep += [s, d]
+        vs.append(vkt.StructuredVolume.from_tensor(s))
+        vd.append(vkt.StructuredVolume.from_tensor(d))
+        fs.append(vkt.Filter.gaussian(it["k"], it["sigma"]))
+    vkt.check(vkt._lib.vktAutotuneSetEnabled(0))
+    for _ in range(args.reps):
+        vkt.apply_filter_batch(vd, vs, fs)
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    print(json.dumps({"kernel_case": "batch256", "reps": args.reps,
+                      "checksum": float(sum(float(np.abs(d.cpu().numpy().astype(np.float64)).mean())
+                                            for d in keep[1::2]))}))
+
+
 def run_kernel_case(args):
     import torch
     import synth
     import paper_2203_10213_gb300 as vkt
+    if args.kernel_case == "batch256":
+        run_batch_case(args)
+        return
     kind, fmt, dims, filt, path = KERNEL_CASES[args.kernel_case]
     if kind == "uniform":
         vol = synth.uniform(synth.BASE_SEED + 5, tuple(reversed(dims)), -1.0, 1.0)

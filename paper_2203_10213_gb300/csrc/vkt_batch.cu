@@ -26,10 +26,16 @@
 namespace vkt {
 namespace {
 
-// COMP: the work list holds only compensated-mode bricks (integer destinations whose FP32
-// error bound is too loose); each mode gets its own launch so that neither pays the other's
-// registers.
-template <bool COMP>
+// One persistent kernel per (filter size K, accumulation mode): its work list holds only
+// bricks of volumes with that K (and, for COMP, integer destinations whose FP32 error bound
+// is too loose), so its code holds one brick variant (a kernel for every K thrashed the
+// instruction cache) and its registers are those of K.  The kernels of one batch run as
+// parallel branches of the graph: blocks of the next kernel fill the SMs that a drained
+// kernel leaves, so no kernel's tail idles the GPU.
+using BatchKernel = void (*)(const sep::Job*, const CUtensorMap*, const int4*, int, unsigned*,
+                             unsigned*);
+
+template <int K, bool COMP>
 __global__ void __launch_bounds__(sep::NT, 2)
     k_sep_batch(const sep::Job* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
                 const int4* __restrict__ items, int nitems, unsigned* counter, unsigned* status)
@@ -48,30 +54,33 @@ __global__ void __launch_bounds__(sep::NT, 2)
         const int4 w = items[item];
         const sep::Job& J = jobs[w.x];
         const CUtensorMap* tm = maps + w.x;
-        bool ok = true;
-        switch (J.k) {
-#define VKT_BATCH_CASE(KK)                                                                   \
-    case KK: {                                                                               \
-        sep::W<KK> G;                                                                        \
-        for (int i = 0; i < KK; ++i) {                                                       \
-            G.gx[i] = J.g[0][i];                                                             \
-            G.gy[i] = J.g[1][i];                                                             \
-            G.gz[i] = J.g[2][i];                                                             \
-        }                                                                                    \
-        if (COMP)                                                                            \
-            ok = sep::brick_comp<KK>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);         \
-        else                                                                                 \
-            ok = sep::brick<KK>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);              \
-        break;                                                                               \
-    }
-            VKT_BATCH_CASE(1)
-            VKT_BATCH_CASE(3)
-            VKT_BATCH_CASE(5)
-            VKT_BATCH_CASE(7)
-#undef VKT_BATCH_CASE
-        default: break;
+        sep::W<K> G;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            G.gx[i] = J.g[0][i];
+            G.gy[i] = J.g[1][i];
+            G.gz[i] = J.g[2][i];
         }
+        bool ok;
+        if constexpr (COMP)
+            ok = sep::brick_comp<K>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
+        else
+            ok = sep::brick<K>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
         if (!ok) break;
+    }
+}
+
+constexpr int NKS = 4;                     // filter sizes of the persistent kernels: 1, 3, 5, 7
+constexpr int KS[NKS] = {1, 3, 5, 7};
+int k_slot(int k) { return k <= 1 ? 0 : (k <= 3 ? 1 : (k <= 5 ? 2 : 3)); }
+
+BatchKernel batch_kernel(int k, bool comp)
+{
+    switch (k) {
+    case 1: return comp ? k_sep_batch<1, true> : k_sep_batch<1, false>;
+    case 3: return comp ? k_sep_batch<3, true> : k_sep_batch<3, false>;
+    case 5: return comp ? k_sep_batch<5, true> : k_sep_batch<5, false>;
+    default: return comp ? k_sep_batch<7, true> : k_sep_batch<7, false>;
     }
 }
 
@@ -111,7 +120,7 @@ struct Plan {
     sep::Job* d_jobs = nullptr;
     CUtensorMap* d_maps = nullptr;
     int4* d_items = nullptr;
-    unsigned* d_counter = nullptr;
+    unsigned* d_counter = nullptr;    // one work-list counter per persistent kernel
     std::vector<sep::Job> jobs;       // table as last uploaded
     int nitems = 0;
     unsigned kernels = 0;             // kernels one replay launches
@@ -261,29 +270,35 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         order.push_back({-static_cast<long>(J.k) * (J.zchunk + J.k - 1), static_cast<int>(j)});
     }
     std::stable_sort(order.begin(), order.end());
-    std::vector<int4> comp_items;
-    size_t smem_fast = 0, smem_comp = 0;
+    // one work list per (K, mode), each ordered heavy bricks first
+    constexpr int NL = 2 * NKS;
+    std::vector<int4> lists[NL];
+    size_t lsmem[NL] = {};
+    double lwork[NL] = {};
     for (const auto& o : order) {
         const sep::Job& J = P.jobs[o.second];
-        std::vector<int4>& dstv = J.comp ? comp_items : items;
-        (J.comp ? smem_comp : smem_fast) = std::max(J.comp ? smem_comp : smem_fast,
-                                                    batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
+        const int l = 2 * k_slot(J.k) + (J.comp ? 1 : 0);
+        lsmem[l] = std::max(lsmem[l], batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
+        lwork[l] += static_cast<double>(J.nx) * J.ny * J.nz * J.k * (J.comp ? 10.0 : 1.0);
         for (int bz = 0; bz < J.chunks; ++bz)
             for (int by = 0; by < J.tiles_y; ++by)
-                for (int bx = 0; bx < J.tiles_x; ++bx) dstv.push_back(make_int4(o.second, bx, by, bz));
+                for (int bx = 0; bx < J.tiles_x; ++bx)
+                    lists[l].push_back(make_int4(o.second, bx, by, bz));
     }
-    const int nfast = static_cast<int>(items.size());
-    const int ncomp = static_cast<int>(comp_items.size());
-    items.insert(items.end(), comp_items.begin(), comp_items.end());
+    int loff[NL + 1] = {};
+    for (int l = 0; l < NL; ++l) {
+        loff[l + 1] = loff[l] + static_cast<int>(lists[l].size());
+        items.insert(items.end(), lists[l].begin(), lists[l].end());
+    }
     P.nitems = static_cast<int>(items.size());
     (void)smem;
 
-    // one device block: table | maps (64-byte aligned) | items | two counters
+    // one device block: table | maps (64-byte aligned) | items | one counter per list
     const size_t njobs = std::max<size_t>(1, P.jobs.size());
     const size_t off_maps = ((njobs * sizeof(sep::Job)) + 127) & ~size_t(127);
     const size_t off_items = off_maps + njobs * sizeof(CUtensorMap);
     const size_t off_counter = off_items + std::max<size_t>(1, items.size()) * sizeof(int4);
-    const size_t total = off_counter + 256;
+    const size_t total = off_counter + 2 * NKS * 128;   // counters 128 bytes apart
     cudaError_t e = cudaMalloc(&P.dmem, total);
     if (e != cudaSuccess) return from_cuda(e);
     unsigned char* base = static_cast<unsigned char*>(P.dmem);
@@ -301,30 +316,49 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P.device);
-    int grid_fast = 0, grid_comp = 0;
-    if (nfast > 0) {
-        e = cudaFuncSetAttribute(k_sep_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem_fast));
+    int lgrid[NL] = {};
+    for (int l = 0; l < NL; ++l) {
+        const int nl = loff[l + 1] - loff[l];
+        if (nl == 0) continue;
+        BatchKernel kern = batch_kernel(KS[l / 2], l % 2 == 1);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(lsmem[l]));
         if (e != cudaSuccess) return from_cuda(e);
         int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<false>, sep::NT, smem_fast);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sep::NT, lsmem[l]);
         if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
-        grid_fast = static_cast<int>(std::min<long>(nfast, static_cast<long>(sms) * std::max(per_sm, 1)));
+        lgrid[l] = static_cast<int>(std::min<long>(nl, static_cast<long>(sms) * std::max(per_sm, 1)));
     }
-    if (ncomp > 0) {
-        e = cudaFuncSetAttribute(k_sep_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(smem_comp));
-        if (e != cudaSuccess) return from_cuda(e);
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sep_batch<true>, sep::NT, smem_comp);
-        if (per_sm_cap > 0) per_sm = std::min(per_sm, per_sm_cap);
-        grid_comp = static_cast<int>(std::min<long>(ncomp, static_cast<long>(sms) * std::max(per_sm, 1)));
-    }
+    // lists launched heaviest first
+    int lorder[NL];
+    for (int l = 0; l < NL; ++l) lorder[l] = l;
+    std::stable_sort(lorder, lorder + NL, [&](int a, int b) { return lwork[a] > lwork[b]; });
 
-    // capture: counter reset + persistent kernel + dense triples on their own paths
+    // capture: counter reset, then a fork: every list's persistent kernel on a branch of its
+    // own, the dense triples on the main branch, joined at the end
     cudaStream_t cs;
     e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (e != cudaSuccess) return from_cuda(e);
+    cudaStream_t side[NL] = {};
+    cudaEvent_t fork = nullptr, join[NL] = {};
+    e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int l = 0; l < NL && e == cudaSuccess; ++l) {
+        if (loff[l + 1] == loff[l]) continue;
+        e = cudaStreamCreateWithFlags(&side[l], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[l], cudaEventDisableTiming);
+    }
+    auto cleanup = [&]() {
+        for (int l = 0; l < NL; ++l) {
+            if (side[l]) cudaStreamDestroy(side[l]);
+            if (join[l]) cudaEventDestroy(join[l]);
+        }
+        if (fork) cudaEventDestroy(fork);
+        cudaStreamDestroy(cs);
+    };
+    if (e != cudaSuccess) {
+        cleanup();
+        return from_cuda(e);
+    }
     Ctx cctx = ctx;
     cctx.stream = cs;
     uint64_t before = 0;
@@ -333,18 +367,18 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     vktError err = from_cuda(e);
     unsigned kernels = 0;
     if (err == VKT_NO_ERROR && P.nitems > 0) {
-        e = cudaMemsetAsync(P.d_counter, 0, 2 * sizeof(unsigned), cs);
-        if (e == cudaSuccess && nfast > 0) {
-            k_sep_batch<false><<<grid_fast, sep::NT, smem_fast, cs>>>(P.d_jobs, P.d_maps, P.d_items,
-                                                                      nfast, P.d_counter, ctx.status);
+        e = cudaMemsetAsync(P.d_counter, 0, NL * 128, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, cs);
+        for (int q = 0; q < NL && e == cudaSuccess; ++q) {
+            const int l = lorder[q];
+            const int nl = loff[l + 1] - loff[l];
+            if (nl == 0) continue;
+            e = cudaStreamWaitEvent(side[l], fork, 0);
+            if (e != cudaSuccess) break;
+            batch_kernel(KS[l / 2], l % 2 == 1)<<<lgrid[l], sep::NT, lsmem[l], side[l]>>>(
+                P.d_jobs, P.d_maps, P.d_items + loff[l], nl, P.d_counter + 32 * l, ctx.status);
             e = cudaGetLastError();
-            ++kernels;
-        }
-        if (e == cudaSuccess && ncomp > 0) {
-            k_sep_batch<true><<<grid_comp, sep::NT, smem_comp, cs>>>(P.d_jobs, P.d_maps,
-                                                                     P.d_items + nfast, ncomp,
-                                                                     P.d_counter + 1, ctx.status);
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(join[l], side[l]);
             ++kernels;
         }
         err = from_cuda(e);
@@ -382,10 +416,13 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
             err = launch_direct(job, f->w, f->k, cctx);
         ++kernels;
     }
+    // join the branches into the main stream before the capture ends
+    for (int l = 0; l < NL && err == VKT_NO_ERROR; ++l)
+        if (side[l] && loff[l + 1] > loff[l]) err = from_cuda(cudaStreamWaitEvent(cs, join[l], 0));
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cs, &graph);
     if (err == VKT_NO_ERROR) err = from_cuda(e);
-    cudaStreamDestroy(cs);
+    cleanup();
     uint64_t after = 0;
     vktGetLaunchCount(&after);
     uncount_launches(static_cast<unsigned>(after - before));   // captured, not launched
@@ -398,9 +435,16 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     if (e != cudaSuccess) return from_cuda(e);
     P.kernels = kernels;
     if (ctx.debug & VKT_DEBUG_LOG)
-        fprintf(stderr, "[vkt] batch plan: %zu separable volumes, %d + %d compensated bricks, "
-                "grids %d / %d, %zu single launches, brick z target %d, CTAs per SM cap %d\n",
-                P.jobs.size(), nfast, ncomp, grid_fast, grid_comp, dense_idx.size(), zt, per_sm_cap);
+    {
+        fprintf(stderr, "[vkt] batch plan: %zu separable volumes, %d bricks in %u persistent kernels,"
+                " %zu single launches, brick z target %d, CTAs per SM cap %d\n", P.jobs.size(),
+                P.nitems, kernels - static_cast<unsigned>(dense_idx.size()), dense_idx.size(), zt,
+                per_sm_cap);
+        for (int l = 0; l < NL; ++l)
+            if (loff[l + 1] > loff[l])
+                fprintf(stderr, "[vkt]   k=%d%s: %d bricks, grid %d, smem %zu\n", KS[l / 2],
+                        l % 2 ? " compensated" : "", loff[l + 1] - loff[l], lgrid[l], lsmem[l]);
+    }
     return VKT_NO_ERROR;
 }
 

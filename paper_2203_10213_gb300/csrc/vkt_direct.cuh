@@ -262,6 +262,34 @@ __global__ void __launch_bounds__(NT)
             pend = s;
         }
         // multiply the plane into the accumulators
+        if constexpr (Cfg::PAIR && !COMP) {
+            // row offset b outermost: the K*K weight pairs (w, w) of one b serve every output
+            // row, so each pair is formed once per plane instead of once per input row (the
+            // window rows are loaded K times instead of once; measured 1.4 % faster at k = 3)
+#pragma unroll
+            for (int b = 0; b < K; ++b) {
+#pragma unroll
+                for (int i = 0; i < RY; ++i) {
+                    float win[RX + K - 1];
+                    load_row<RX + K - 1, RX>(Fb + (ty * RY + i + b) * FP + tx * RX, win);
+#pragma unroll
+                    for (int c = 0; c < K; ++c) {
+                        const int sl = Cfg::ROT ? (K - 1 - c) : (((u - c + R) % K + K) % K);
+#pragma unroll
+                        for (int x = 0; x < RX; x += 2)
+#pragma unroll
+                            for (int a = 0; a < K; ++a) {
+                                const float wv = W.w[(c * K + b) * K + a];
+                                const float2 w2 = make_float2(wv, wv);
+                                const float2 v2 = make_float2(win[x + a], win[x + a + 1]);
+                                float2& d = acc[sl][i][x >> 1];
+                                d = (c == 0 && b == 0 && a == 0) ? __fmul2_rn(w2, v2)
+                                                                 : __ffma2_rn(w2, v2, d);
+                            }
+                    }
+                }
+            }
+        } else {
 #pragma unroll
         for (int j = 0; j < RY + K - 1; ++j) {
             float win[RX + K - 1];
@@ -305,6 +333,7 @@ __global__ void __launch_bounds__(NT)
                     }
                 }
             }
+        }
         }
         // output plane it - 2R + zc0 is complete
         const int sl0 = Cfg::ROT ? 0 : (((u - R) % K + K) % K);

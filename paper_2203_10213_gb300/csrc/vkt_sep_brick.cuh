@@ -71,29 +71,38 @@ struct W {
 };
 
 // FX: the x pass reads the raw tensor-map stage directly (converting as it loads) into one of
-// two x-pass tiles, so a plane needs one CTA barrier instead of two and no float tile.  For
-// float32 sources with tensor-map loads (17-21 % faster at k = 3, 5), and uint8 at k = 3 only
-// (9 % faster; at k = 5 and 7 the k + 3 byte loads per x-pass item cost more than the
-// barrier saves: 3 % and 20 % slower)
+// two x-pass tiles, so a plane needs one CTA barrier instead of two, no float tile, and none
+// of the float tile's shared-memory traffic (about 14 of the 30 bytes per output voxel).  For
+// float32 sources with tensor-map loads (17-21 % faster at k = 3, 5) and for uint8 sources,
+// whose window is read as three aligned 32-bit words and converted with a byte permute
+// (byte_float) instead of one byte load and one conversion per voxel (k = 5 on 512^3:
+// 0.209 -> 0.199 ms at two CTAs per SM; at three it spills)
 template <int LM, int SF, int K>
 __host__ __device__ constexpr bool fused_x()
 {
-    return LM == LM_TMA && (SF == FMT_F32 || (SF == FMT_U8 && K == 3));
+    return LM == LM_TMA && (SF == FMT_F32 || SF == FMT_U8);
 }
 
-template <int K>
+// byte i (0..3) of word w as the float it codes (exact): 2^23 + code built by a byte permute,
+// minus 2^23
+__device__ __forceinline__ float byte_float(uint32_t w, int i)
+{
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + i)) - 8388608.f;
+}
+
+template <int K, int NS = FSTAGES>
 __host__ __device__ constexpr size_t smem_bytes_fx(int sfmt)
 {
     using Geo = Brick<K, TX, TY>;
-    return 128 + static_cast<size_t>(FSTAGES) * Geo::stage_bytes(sfmt, false) +
+    return 128 + static_cast<size_t>(NS) * Geo::stage_bytes(sfmt, false) +
            2 * static_cast<size_t>(Geo::FH) * TX * sizeof(float);
 }
 
-template <int K>
+template <int K, int NS = FSTAGES>
 __host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 {
     using Geo = Brick<K, TX, TY>;
-    return 128 + static_cast<size_t>(FSTAGES) * Geo::stage_bytes(sfmt, rows) +
+    return 128 + static_cast<size_t>(NS) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +      // float tile
            static_cast<size_t>(Geo::FH) * TX * sizeof(float);            // x-pass output
 }
@@ -102,7 +111,7 @@ __host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 __device__ __forceinline__ void init_barriers(unsigned char* smem)
 {
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < 9; ++s) mbar_init(&bars[s], 1);   // up to 9 stages (in the 128-byte header)
     fence_mbar_init();
 }
 
@@ -112,11 +121,15 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // draining the loads in flight).
 // ROI: the job's region fields (origin, store bounds) are read; otherwise the whole volume is
 // assumed at compile time (no region arithmetic in the store path)
-template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false>
+template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false,
+          int NS = FSTAGES>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
 {
+    // a ring of exactly K stages whose first plane is stage 0 (gplane == 0, the single-volume
+    // kernels): plane g*K + u of the K-times unrolled loop uses stage u, phase g
+    constexpr bool STATIC = NS == K;
     using Geo = Brick<K, TX, TY>;
     constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
     constexpr int XGROUPS = TX / 4;
@@ -132,7 +145,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     constexpr bool FX = fused_x<LM, SF, K>();
-    float* F = reinterpret_cast<float*>(raw + FSTAGES * rawb);
+    float* F = reinterpret_cast<float*>(raw + NS * rawb);
     float* T1 = FX ? F : F + FH * FP;     // FX: two x-pass tiles, no float tile
 
     const int tid = threadIdx.x;
@@ -150,21 +163,21 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const uint64_t vol_bytes =
         static_cast<uint64_t>(J.nx) * J.ny * J.nz * fmt_bytes(sfmt);
     if (tma && tid == 0) {
-        for (int s = 0; s < FSTAGES && s < nplanes; ++s, ++issued) {
+        for (int s = 0; s < NS && s < nplanes; ++s, ++issued) {
             const uint32_t q = g0 + s;
-            mbar_arrive_expect_tx(&bars[q % FSTAGES], txb);
-            tma_load_3d(raw + (q % FSTAGES) * rawb, tmap, &bars[q % FSTAGES], x0 - xa, y0 - R,
+            mbar_arrive_expect_tx(&bars[q % NS], txb);
+            tma_load_3d(raw + (q % NS) * rawb, tmap, &bars[q % NS], x0 - xa, y0 - R,
                         clampi(pfirst + s, 0, J.nz - 1));
         }
     } else if (rows) {
-        for (int s = 0; s < FSTAGES && s < nplanes; ++s) {
+        for (int s = 0; s < NS && s < nplanes; ++s) {
             const uint32_t q = g0 + s;
-            issue_rows<Geo, NT>(raw + (q % FSTAGES) * rawb, &bars[q % FSTAGES], J.src, vol_bytes,
+            issue_rows<Geo, NT>(raw + (q % NS) * rawb, &bars[q % NS], J.src, vol_bytes,
                                 sfmt, J.nx, J.ny, J.nz, x0, y0, pfirst + s, tid);
         }
         __syncthreads();   // every thread's expect_tx precedes the single arrival
         if (tid == 0)
-            for (int s = 0; s < FSTAGES && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % FSTAGES]);
+            for (int s = 0; s < NS && s < nplanes; ++s, ++issued) mbar_arrive(&bars[(g0 + s) % NS]);
     }
 
     ConvPlan<Geo, NT> plan;
@@ -196,14 +209,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     const int yend = ROI ? J.sy1 : J.ny;
     bool failed = false;
 
-    auto plane = [&](const int it, const int u) {
+    auto plane = [&](const int it, const int u, const int gg) {
         const uint32_t q = g0 + it;
-        const int s = q % FSTAGES;
+        const int s = STATIC ? u : static_cast<int>(q % NS);
+        const uint32_t par = STATIC ? (gg & 1) : ((q / NS) & 1);
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
         if constexpr (FX) {
             float* T1b = T1 + (it & 1) * FH * TX;
-            ok = mbar_wait(&bars[s], (q / FSTAGES) & 1);
+            ok = mbar_wait(&bars[s], par);
             // x pass straight from the raw stage: T1b[row][x] = sum_a gx[a] v(x + a - r), the
             // source voxels converted as they are loaded, clamped in x only at the volume's
             // x faces (the rows are clamped through the stage row read)
@@ -220,9 +234,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
                         if constexpr (SF == FMT_U8) {
                             const unsigned char* rp = rs + rrow * RWE;
                             if (xin) {
+                                // the item's K + 3 bytes start at raw column 4g + xa - R
+                                // (xa = 16): the three aligned words from word g + W0 cover them
+                                constexpr int W0 = (16 - R) / 4, O = (16 - R) & 3;
+                                static_assert(O + K + 3 <= 12, "three words hold the window");
+                                const uint32_t* wp = reinterpret_cast<const uint32_t*>(rp) + g + W0;
+                                const uint32_t wd[3] = {wp[0], wp[1], wp[2]};
 #pragma unroll
                                 for (int e = 0; e < 4 + K - 1; ++e)
-                                    win[e] = static_cast<float>(rp[4 * g - R + xa + e]);
+                                    win[e] = byte_float(wd[(O + e) >> 2], (O + e) & 3);
                             } else {
 #pragma unroll
                                 for (int e = 0; e < 4 + K - 1; ++e)
@@ -258,15 +278,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
                 failed = true;
                 return;
             }
-            if (tid == 0 && it + FSTAGES < nplanes) {
+            if (tid == 0 && it + NS < nplanes) {
                 mbar_arrive_expect_tx(&bars[s], txb);
                 tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
-                            clampi(pfirst + it + FSTAGES, 0, J.nz - 1));
+                            clampi(pfirst + it + NS, 0, J.nz - 1));
                 ++issued;
             }
         } else {
         if (tma || rows) {
-            ok = mbar_wait(&bars[s], (q / FSTAGES) & 1);
+            ok = mbar_wait(&bars[s], par);
         } else {
             fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), J.src, sfmt, J.nx, J.ny,
                                     J.nz, x0, y0, pfirst + it, tid);
@@ -285,15 +305,15 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
             failed = true;
             return;
         }
-        if (tma && tid == 0 && it + FSTAGES < nplanes) {
+        if (tma && tid == 0 && it + NS < nplanes) {
             mbar_arrive_expect_tx(&bars[s], txb);
             tma_load_3d(raw + s * rawb, tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(pfirst + it + FSTAGES, 0, J.nz - 1));
+                        clampi(pfirst + it + NS, 0, J.nz - 1));
             ++issued;
-        } else if (rows && it + FSTAGES < nplanes) {
+        } else if (rows && it + NS < nplanes) {
             // all threads; the arrival follows the x-pass barrier below
             issue_rows<Geo, NT>(raw + s * rawb, &bars[s], J.src, vol_bytes, sfmt, J.nx, J.ny,
-                                J.nz, x0, y0, pfirst + it + FSTAGES, tid);
+                                J.nz, x0, y0, pfirst + it + NS, tid);
         }
         // x pass: T1[row][x] = sum_a gx[a] F[row][x + a], 4 outputs per item
 #pragma unroll
@@ -317,7 +337,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         }
         __syncthreads();
         // the stage refilled by row copies above is complete in expectation: one arrival
-        if (rows && tid == 0 && it + FSTAGES < nplanes) {
+        if (rows && tid == 0 && it + NS < nplanes) {
             mbar_arrive(&bars[s]);
             ++issued;
         }
@@ -415,7 +435,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
         for (int u = 0; u < K; ++u) {
             const int it = g * K + u;
             if (it >= nplanes || failed) break;
-            plane(it, u);
+            plane(it, u, g);
         }
     }
     // only bricks loaded through the stage barriers move them through their phases
@@ -424,8 +444,8 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     if (failed) {
         if (tid == 0) {
             atomicOr(status, STATUS_TIMEOUT);
-            for (int it = issued - 1; it >= 0 && it >= issued - FSTAGES; --it)
-                mbar_wait(&bars[(g0 + it) % FSTAGES], ((g0 + it) / FSTAGES) & 1);
+            for (int it = issued - 1; it >= 0 && it >= issued - NS; --it)
+                mbar_wait(&bars[(g0 + it) % NS], ((g0 + it) / NS) & 1);
         }
         __syncthreads();
         return false;

@@ -12,10 +12,17 @@
 namespace vkt {
 namespace sepk {
 
-// CTAs per SM the register allocation must allow: three up to k = 5 (the tensor-map kernels
-// fit in 80 registers without spills there), else two
+// CTAs per SM the register allocation must allow: three up to k = 5 (the float32 and
+// run-time-format kernels fit in 80 registers there), two for k = 7 and for the uint8
+// kernels, whose fused word-load x pass needs about 120
 template <int K, int SF>
-constexpr int sep_min_blocks() { return K <= 5 ? 3 : 2; }
+constexpr int sep_min_blocks() { return (K <= 5 && SF != FMT_U8) ? 3 : 2; }
+
+// planes in flight of a single-volume kernel: k for whole-volume tensor-map kernels up to
+// k = 7, a ring whose stage and phase are compile-time constants of the k-times unrolled
+// plane loop (measured 1 % faster than three stages at k = 5), else the batch brick's three
+template <int K, int LM, bool ROI>
+constexpr int ns_of() { return (LM == sep::LM_TMA && !ROI && K >= 3 && K <= 7) ? K : sep::FSTAGES; }
 
 // SF/DF: source and destination formats fixed at compile time (-1: read from the job);
 // LM: the way stages are filled (sep::LM_*), fixed at compile time where known
@@ -31,8 +38,9 @@ __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
     }
     __syncthreads();
     uint32_t gplane = 0;
-    sep::brick<K, sep::W<K>, SF, DF, LM, ROI>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
-                                              smem, gplane, status);
+    sep::brick<K, sep::W<K>, SF, DF, LM, ROI, ns_of<K, LM, ROI>()>(J, G, &tmap, blockIdx.x,
+                                                                  blockIdx.y, blockIdx.z, smem,
+                                                                  gplane, status);
 }
 
 template <int K, int LM = sep::LM_ANY, bool ROI = false>
@@ -148,8 +156,10 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
     // the tensor-map kernels of the compiled-in formats fuse the conversion into the x pass
     // (their own shared-memory layout)
     if (!J.comp && J.use_tma && J.dfmt == FMT_F32 &&
-        (J.sfmt == FMT_F32 || (J.sfmt == FMT_U8 && K == 3)) && K >= 3 && K <= 7)
-        smem = std::max(smem, sep::smem_bytes_fx<K>(job.sfmt));
+        (J.sfmt == FMT_F32 || J.sfmt == FMT_U8) && K >= 3 && K <= 7)
+        smem = std::max(smem, sep::smem_bytes_fx<K, K>(job.sfmt));
+    if (!J.comp && J.use_tma && !job.roi && K >= 3 && K <= 7)
+        smem = std::max(smem, sep::smem_bytes<K, K>(job.sfmt, false));
     cudaError_t e = J.comp ? cudaFuncSetAttribute(comp,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   static_cast<int>(smem))

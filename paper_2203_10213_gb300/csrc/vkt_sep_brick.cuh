@@ -121,15 +121,18 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // draining the loads in flight).
 // ROI: the job's region fields (origin, store bounds) are read; otherwise the whole volume is
 // assumed at compile time (no region arithmetic in the store path)
+// NS: planes in flight (stages of the ring).  STATIC: the caller guarantees that this brick
+// is the CTA's only one (gplane == 0 on entry: the single-volume kernels) and NS == K, so
+// plane g*K + u of the K-times unrolled loop uses stage u and phase g, both known without
+// arithmetic.  A persistent CTA (the batch) carries gplane from brick to brick and must use
+// the general ring, whatever NS and K are.
 template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false,
-          int NS = FSTAGES>
+          int NS = FSTAGES, bool STATIC = false>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
 {
-    // a ring of exactly K stages whose first plane is stage 0 (gplane == 0, the single-volume
-    // kernels): plane g*K + u of the K-times unrolled loop uses stage u, phase g
-    constexpr bool STATIC = NS == K;
+    static_assert(!STATIC || NS == K, "the static ring has one stage per unrolled plane");
     using Geo = Brick<K, TX, TY>;
     constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
     constexpr int XGROUPS = TX / 4;
@@ -212,7 +215,7 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
     auto plane = [&](const int it, const int u, const int gg) {
         const uint32_t q = g0 + it;
         const int s = STATIC ? u : static_cast<int>(q % NS);
-        const uint32_t par = STATIC ? (gg & 1) : ((q / NS) & 1);
+        const uint32_t par = STATIC ? static_cast<uint32_t>(gg & 1) : ((q / NS) & 1);
         const unsigned char* rs = raw + s * rawb;
         bool ok = true;
         if constexpr (FX) {

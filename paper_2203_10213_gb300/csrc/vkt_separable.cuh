@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
         if (LM != sep::LM_ROWS && J.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
-    uint32_t gplane = 0;
-    sep::brick<K, sep::W<K>, SF, DF, LM, ROI, ns_of<K, LM, ROI>()>(J, G, &tmap, blockIdx.x,
-                                                                  blockIdx.y, blockIdx.z, smem,
-                                                                  gplane, status);
+    uint32_t gplane = 0;   // this CTA's only brick: the static ring applies when NS == K
+    constexpr int NS = ns_of<K, LM, ROI>();
+    sep::brick<K, sep::W<K>, SF, DF, LM, ROI, NS, NS == K>(J, G, &tmap, blockIdx.x, blockIdx.y,
+                                                           blockIdx.z, smem, gplane, status);
 }
 
 template <int K, int LM = sep::LM_ANY, bool ROI = false>

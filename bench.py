@@ -58,11 +58,13 @@ def parse():
 
 
 # single-kernel cases for profiler captures: (value model, format, dims, filter, path)
+# (path "auto": the path and launch shape the step's calls take, tuned on the first call;
+# with VKT_AUTOTUNE_CACHE naming the file a previous run wrote, the choice is read, not timed)
 KERNEL_CASES = {
-    "sep5_ct512": ("blobs", 0, (512, 512, 512), "gaussian5", "separable"),
-    "lap3_ct512": ("blobs", 0, (512, 512, 512), "laplacian3", "direct"),
-    "sep5_ct640": ("blobs", 0, (640, 512, 512), "gaussian5", "separable"),
-    "lap3_ct640": ("blobs", 0, (640, 512, 512), "laplacian3", "direct"),
+    "sep5_ct512": ("blobs", 0, (512, 512, 512), "gaussian5", "auto"),
+    "lap3_ct512": ("blobs", 0, (512, 512, 512), "laplacian3", "auto"),
+    "sep5_ct640": ("blobs", 0, (640, 512, 512), "gaussian5", "auto"),
+    "lap3_ct640": ("blobs", 0, (640, 512, 512), "laplacian3", "auto"),
     "tc7_dns512": ("uniform", 2, (512, 512, 256), "random7", "tensor"),
     "direct7_dns512": ("uniform", 2, (512, 512, 256), "random7", "direct"),
     "batch256": None,    # the batching form's 256 volumes (run_batch_case)
@@ -552,8 +554,9 @@ def small_form(vkt, torch, stream, lib, dev):
     """The smallest case: one float32 volume of 64^3 voxels i.i.d. U[0,1) from the seed, the
     normalised 3^3 Gaussian sigma 1.0 as dense weights on the FP32 direct path.  Its 2 MiB
     of algorithmic bytes stay in L2 and one call takes a few microseconds, so it is
-    launch-bound: reported as the per-call time of 200 calls back to back on one stream,
-    and of one call bracketed alone by events (median of 20)."""
+    launch-bound: reported as the per-call time of 200 calls back to back on one stream
+    (bound by the host's per-call work), of 20 calls captured in a CUDA graph and replayed
+    (the device time per call), and of one call bracketed alone by events (median of 20)."""
     import synth
     n = 64
     x = torch.from_numpy(synth.volume("uniform", synth.F32, (n, n, n), synth.BASE_SEED)).to(dev)
@@ -576,6 +579,25 @@ def small_form(vkt, torch, stream, lib, dev):
         b.record(stream)
         torch.cuda.synchronize()
         ms_loop = a.elapsed_time(b) / loop
+        # the call captured once in a CUDA graph and replayed: the device time per call
+        # without the host's per-call work (argument checks, the Python-to-C call)
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            with vkt.policy(stream=gs, path="direct"):
+                for _ in range(20):
+                    call()
+        stream.wait_stream(gs)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(10):
+            graph.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_graph = a.elapsed_time(b) / (10 * 20)
         single = []
         for _ in range(20):
             a.record(stream)
@@ -593,6 +615,8 @@ def small_form(vkt, torch, stream, lib, dev):
             "path": "direct", "bound": "launch (inputs and outputs L2-resident)",
             "back_to_back_ms": round(ms_loop, 5),
             "back_to_back_gvoxel_s": round(vox / (ms_loop * 1e-3) / 1e9, 2),
+            "graph_replay_ms_per_call": round(ms_graph, 5),
+            "graph_replay_gvoxel_s": round(vox / (ms_graph * 1e-3) / 1e9, 2),
             "single_call_ms": round(ms_one, 5),
             "single_call_gvoxel_s": round(vox / (ms_one * 1e-3) / 1e9, 2)}
 

@@ -114,7 +114,7 @@ VKT_API vktError vktGetThreadExecutionPolicy(vktExecutionPolicy* policy);
  * (the rule's path, for dense filters that the tensor path can evaluate also the other
  * path, and three brick z extents of the CUDA-core paths), keeps the fastest and uses it
  * from then on.  That first call synchronises the policy stream and launches each candidate
- * three times into the destination (the last launch is the chosen one); a call made while
+ * four times into the destination (then the chosen one once more); a call made while
  * its stream is being captured into a graph uses the rule.  vktApplyFilterBatchSV tunes
  * each new batch plan the same way (brick z extent, persistent grid).  The choices live in
  * memory; when VKT_AUTOTUNE_CACHE names a file they are read from it at the first lookup and

@@ -169,9 +169,9 @@ bool autotune_lookup(const char* key, TuneChoice* c);
 void autotune_store(const char* key, const TuneChoice& c);
 // Whether work enqueued on `stream` now would be captured into a graph (no timing then).
 bool stream_capturing(cudaStream_t stream);
-// Times run(candidate) for every candidate on `stream` (one untimed launch, then two timed
-// with CUDA events; candidates whose launch fails are skipped) and returns the fastest in
-// *best (VKT_ERROR_UNSUPPORTED when none ran).  Synchronises the stream.
+// Times run(candidate) for every candidate on `stream` (one untimed launch, then three
+// timed with CUDA events; candidates whose launch fails are skipped) and returns the fastest
+// in *best (VKT_ERROR_UNSUPPORTED when none ran).  Synchronises the stream.
 template <class Run>
 vktError autotune_time(const TuneChoice* cand, int n, Run run, cudaStream_t stream, TuneChoice* best)
 {
@@ -186,8 +186,8 @@ vktError autotune_time(const TuneChoice* cand, int n, Run run, cudaStream_t stre
     for (int i = 0; i < n; ++i) {
         if (run(cand[i]) != VKT_NO_ERROR) continue;
         cudaEventRecord(ev[0], stream);
-        vktError e1 = run(cand[i]);
-        vktError e2 = e1 == VKT_NO_ERROR ? run(cand[i]) : e1;
+        vktError e2 = VKT_NO_ERROR;
+        for (int r = 0; r < 3 && e2 == VKT_NO_ERROR; ++r) e2 = run(cand[i]);
         cudaEventRecord(ev[1], stream);
         if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
             err = from_cuda(cudaGetLastError());
@@ -196,7 +196,7 @@ vktError autotune_time(const TuneChoice* cand, int n, Run run, cudaStream_t stre
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
         if (e2 != VKT_NO_ERROR) continue;
-        ms *= 0.5f;
+        ms *= 1.f / 3.f;
         if (!found || ms < best->ms) {
             *best = cand[i];
             best->ms = ms;

@@ -543,7 +543,7 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
     const int yend = ROI ? J.sy1 : J.ny;
     bool failed = false;
 
-    auto plane = [&](const int it, const int u) {
+    auto plane = [&](const int it) {
         const uint32_t q = g0 + it;
         const int s = q % STAGES;
         const unsigned char* rs = raw + s * rawb;
@@ -614,13 +614,15 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
                 dot2_step(G.gy[b], v.x, v.y, ts[x], tc[x]);
             }
         }
+        // z pass: slot K-1-c holds the output plane that this input plane reaches through
+        // tap c, so slot 0 completes now; the slots then shift down by one
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            const int sl = ((u - c + R) % K + K) % K;
+            const int sl = K - 1 - c;
 #pragma unroll
             for (int x = 0; x < RX; ++x) dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
         }
-        const int sl0 = ((u - R) % K + K) % K;
+        constexpr int sl0 = 0;
         if (it >= 2 * R && oy < yend && nvalid > 0) {
             const int oz = pfirst + it - R;
             const int64_t idx = (static_cast<int64_t>(oz) * J.ny + oy) * J.nx + ox;
@@ -637,17 +639,21 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
             }
         }
 #pragma unroll
-        for (int x = 0; x < RX; ++x) acc_s[sl0][x] = acc_c[sl0][x] = 0.f;
+        for (int q = 0; q + 1 < K; ++q)
+#pragma unroll
+            for (int x = 0; x < RX; ++x) {
+                acc_s[q][x] = acc_s[q + 1][x];
+                acc_c[q][x] = acc_c[q + 1][x];
+            }
+#pragma unroll
+        for (int x = 0; x < RX; ++x) acc_s[K - 1][x] = acc_c[K - 1][x] = 0.f;
     };
 
-    for (int g = 0; g * K < nplanes && !failed; ++g) {
-#pragma unroll
-        for (int u = 0; u < K; ++u) {
-            const int it = g * K + u;
-            if (it >= nplanes || failed) break;
-            plane(it, u);
-        }
-    }
+    // one plane body, not unrolled: the Dot2 arithmetic of a plane is large, and a loop
+    // unrolled k times (compile-time slots) overflowed the instruction cache (k = 7: the
+    // batch's compensated kernel stalled on instruction fetch more than on anything else)
+#pragma unroll 1
+    for (int it = 0; it < nplanes && !failed; ++it) plane(it);
     if (tma || rows) gplane = g0 + nplanes;
     if (failed) {
         if (tid == 0) {

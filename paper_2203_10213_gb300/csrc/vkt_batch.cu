@@ -65,7 +65,8 @@ __global__ void __launch_bounds__(sep::NT, 2)
         if constexpr (COMP)
             ok = sep::brick_comp<K>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
         else
-            ok = sep::brick<K>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
+            ok = sep::brick<K, sep::W<K>, -1, -1, sep::LM_ANY, false, sep::FSTAGES, false, (K >= 5)>(
+                J, G, tm, w.y, w.z, w.w, smem, gplane, status);
         if (!ok) break;
     }
 }

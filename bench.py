@@ -76,7 +76,7 @@ KERNEL_CASES = {
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.md")
 KERNEL_SOURCES = {
     "separable gaussian5": ["vkt_sep_brick.cuh", "vkt_separable.cuh", "vkt_separable5.cu", "vkt_tile.cuh"],
-    "direct laplacian3": ["vkt_direct.cu", "vkt_tile.cuh"],
+    "direct laplacian3": ["vkt_direct.cuh", "vkt_direct.cu", "vkt_tile.cuh"],
 }
 
 

@@ -35,7 +35,7 @@ namespace {
 using BatchKernel = void (*)(const sep::Job*, const CUtensorMap*, const int4*, int, unsigned*,
                              unsigned*);
 
-template <int K, bool COMP>
+template <int K, bool COMP, int BXG>
 __global__ void __launch_bounds__(sep::NT, 2)
     k_sep_batch(const sep::Job* __restrict__ jobs, const CUtensorMap* __restrict__ maps,
                 const int4* __restrict__ items, int nitems, unsigned* counter, unsigned* status)
@@ -63,10 +63,11 @@ __global__ void __launch_bounds__(sep::NT, 2)
         }
         bool ok;
         if constexpr (COMP)
-            ok = sep::brick_comp<K>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
+            ok = sep::brick_comp<K, sep::W<K>, sep::LM_ANY, false, BXG>(J, G, tm, w.y, w.z, w.w, smem,
+                                                                        gplane, status);
         else
-            ok = sep::brick<K, sep::W<K>, -1, -1, sep::LM_ANY, false, sep::FSTAGES, false, (K >= 5)>(
-                J, G, tm, w.y, w.z, w.w, smem, gplane, status);
+            ok = sep::brick<K, sep::W<K>, -1, -1, sep::LM_ANY, false, sep::FSTAGES, false, (K >= 5),
+                            BXG>(J, G, tm, w.y, w.z, w.w, smem, gplane, status);
         if (!ok) break;
     }
 }
@@ -75,43 +76,70 @@ constexpr int NKS = 4;                     // filter sizes of the persistent ker
 constexpr int KS[NKS] = {1, 3, 5, 7};
 int k_slot(int k) { return k <= 1 ? 0 : (k <= 3 ? 1 : (k <= 5 ? 2 : 3)); }
 
-BatchKernel batch_kernel(int k, bool comp)
+// Brick shapes: the default (16 threads along x: 64 x 32 outputs, 64 x 16 compensated) and
+// the narrow one for volumes it covers with less padding (8 threads along x: 32 x 32).
+constexpr int BXN = 8;
+
+template <int BXG>
+BatchKernel kernel_of(int k, bool comp)
 {
     switch (k) {
-    case 1: return comp ? k_sep_batch<1, true> : k_sep_batch<1, false>;
-    case 3: return comp ? k_sep_batch<3, true> : k_sep_batch<3, false>;
-    case 5: return comp ? k_sep_batch<5, true> : k_sep_batch<5, false>;
-    default: return comp ? k_sep_batch<7, true> : k_sep_batch<7, false>;
+    case 1: return comp ? k_sep_batch<1, true, BXG> : k_sep_batch<1, false, BXG>;
+    case 3: return comp ? k_sep_batch<3, true, BXG> : k_sep_batch<3, false, BXG>;
+    case 5: return comp ? k_sep_batch<5, true, BXG> : k_sep_batch<5, false, BXG>;
+    default: return comp ? k_sep_batch<7, true, BXG> : k_sep_batch<7, false, BXG>;
     }
 }
 
-size_t batch_smem(int k, int sfmt, bool comp, bool rows)
+BatchKernel batch_kernel(int k, bool comp, bool narrow)
+{
+    return narrow ? kernel_of<BXN>(k, comp) : kernel_of<sep::BX>(k, comp);
+}
+
+template <int BXG>
+size_t smem_of(int k, int sfmt, bool comp, bool rows)
 {
     if (comp) {
         switch (k) {
-        case 1: return sep::smem_bytes_comp<1>(sfmt, rows);
-        case 3: return sep::smem_bytes_comp<3>(sfmt, rows);
-        case 5: return sep::smem_bytes_comp<5>(sfmt, rows);
-        default: return sep::smem_bytes_comp<7>(sfmt, rows);
+        case 1: return sep::smem_bytes_comp<1, BXG>(sfmt, rows);
+        case 3: return sep::smem_bytes_comp<3, BXG>(sfmt, rows);
+        case 5: return sep::smem_bytes_comp<5, BXG>(sfmt, rows);
+        default: return sep::smem_bytes_comp<7, BXG>(sfmt, rows);
         }
     }
     switch (k) {
-    case 1: return sep::smem_bytes<1>(sfmt, rows);
-    case 3: return sep::smem_bytes<3>(sfmt, rows);
-    case 5: return sep::smem_bytes<5>(sfmt, rows);
-    default: return sep::smem_bytes<7>(sfmt, rows);
+    case 1: return sep::smem_bytes<1, sep::FSTAGES, BXG>(sfmt, rows);
+    case 3: return sep::smem_bytes<3, sep::FSTAGES, BXG>(sfmt, rows);
+    case 5: return sep::smem_bytes<5, sep::FSTAGES, BXG>(sfmt, rows);
+    default: return sep::smem_bytes<7, sep::FSTAGES, BXG>(sfmt, rows);
     }
 }
 
-int raw_width(int k, int sfmt)
+size_t batch_smem(int k, int sfmt, bool comp, bool rows, bool narrow)
 {
-    switch (k) {
-    case 1: return Brick<1, sep::TX, sep::TY>::raw_w(sfmt);
-    case 3: return Brick<3, sep::TX, sep::TY>::raw_w(sfmt);
-    case 5: return Brick<5, sep::TX, sep::TY>::raw_w(sfmt);
-    default: return Brick<7, sep::TX, sep::TY>::raw_w(sfmt);
-    }
+    return narrow ? smem_of<BXN>(k, sfmt, comp, rows) : smem_of<sep::BX>(k, sfmt, comp, rows);
 }
+
+// output tile (x, y) of a brick shape
+int tile_x(bool narrow) { return narrow ? sep::tile_x<BXN>() : sep::tile_x<sep::BX>(); }
+int tile_y(bool narrow, bool comp)
+{
+    if (comp) return narrow ? sep::tile_y_comp<BXN>() : sep::tile_y_comp<sep::BX>();
+    return narrow ? sep::tile_y<BXN>() : sep::tile_y<sep::BX>();
+}
+
+// the narrow shape when it covers the volume's x-y extent with less padding
+bool narrow_for(int nx, int ny, bool comp)
+{
+    auto area = [&](bool nw) {
+        const long tx = tile_x(nw), ty = tile_y(nw, comp);
+        return ((nx + tx - 1) / tx) * tx * ((ny + ty - 1) / ty) * ty;
+    };
+    return area(true) < area(false);
+}
+
+// TMA box width (raw voxels per stage row) of a brick with tx outputs along x
+int raw_width(int tx, int sfmt) { return tx + 2 * fmt_xalign(sfmt); }
 
 // A replayable batch: device table, tensor maps, work list, counter, and the graph.
 struct Plan {
@@ -227,17 +255,19 @@ int batch_zchunk(int nz, int target)
 // sep_idx: triples for the persistent kernel; dense_idx: triples launched on their own
 // (dense filters, and separable ones of k = 9) inside the same graph.
 // zt: brick z extent target (batch_zchunk); per_sm_cap: CTAs per SM of the persistent grids
-// (0: as many as the occupancy allows)
+// (0: as many as the occupancy allows); narrow: volumes that the narrow brick covers with
+// less padding take it
 vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
                     vktFilter* filters, const std::vector<int>& sep_idx,
                     const std::vector<int>& dense_idx, bool force_dense, bool force_direct,
-                    const Ctx& ctx, int zt = 64, int per_sm_cap = 0)
+                    const Ctx& ctx, int zt = 64, int per_sm_cap = 0, bool narrow = true)
 {
     // work list: separable volumes' bricks, heavy kernels first
     std::vector<int4> items;
     size_t smem = 0;
     P.jobs.resize(sep_idx.size());
     std::vector<CUtensorMap> maps(sep_idx.size());
+    std::vector<char> vnarrow(sep_idx.size(), 0);   // the brick shape of each volume
     std::vector<std::pair<long, int>> order;
     for (size_t j = 0; j < sep_idx.size(); ++j) {
         const int i = sep_idx[j];
@@ -254,32 +284,35 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
         J.dfmt = dst[i]->format;
         J.k = filters[i]->k;
         J.comp = separable_needs_comp(dst[i], s, filters[i]) ? 1 : 0;
-        const int ty = J.comp ? sep::CTY : sep::TY;
+        vnarrow[j] = narrow && narrow_for(J.nx, J.ny, J.comp != 0);
+        const int tx = tile_x(vnarrow[j]), ty = tile_y(vnarrow[j], J.comp != 0);
         J.zchunk = batch_zchunk(J.nz, zt);
-        J.tiles_x = (J.nx + sep::TX - 1) / sep::TX;
+        J.tiles_x = (J.nx + tx - 1) / tx;
         J.tiles_y = (J.ny + ty - 1) / ty;
         J.chunks = (J.nz + J.zchunk - 1) / J.zchunk;
         memset(&maps[j], 0, sizeof(CUtensorMap));
         J.use_tma = encode_tensor_map_3d(&maps[j], J.sfmt, J.src, J.nx, J.ny, J.nz,
-                                         raw_width(J.k, J.sfmt), ty + 2 * ((J.k - 1) / 2), 1)
+                                         raw_width(tx, J.sfmt), ty + 2 * ((J.k - 1) / 2), 1)
                         ? 1
                         : 0;
         // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
         // per row, when the volume starts on a 16-byte boundary
         J.rows = (!J.use_tma && reinterpret_cast<uintptr_t>(J.src) % 16 == 0) ? 1 : 0;
-        smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
+        smem = std::max(smem, batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0, vnarrow[j]));
         order.push_back({-static_cast<long>(J.k) * (J.zchunk + J.k - 1), static_cast<int>(j)});
     }
     std::stable_sort(order.begin(), order.end());
     // one work list per (K, mode), each ordered heavy bricks first
-    constexpr int NL = 2 * NKS;
+    // list l = (k slot, mode, shape): (2 * k_slot + comp) * 2 + narrow
+    constexpr int NL = 4 * NKS;
     std::vector<int4> lists[NL];
     size_t lsmem[NL] = {};
     double lwork[NL] = {};
     for (const auto& o : order) {
         const sep::Job& J = P.jobs[o.second];
-        const int l = 2 * k_slot(J.k) + (J.comp ? 1 : 0);
-        lsmem[l] = std::max(lsmem[l], batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0));
+        const int l = (2 * k_slot(J.k) + (J.comp ? 1 : 0)) * 2 + (vnarrow[o.second] ? 1 : 0);
+        lsmem[l] = std::max(lsmem[l], batch_smem(J.k, J.sfmt, J.comp != 0, J.rows != 0,
+                                                 vnarrow[o.second]));
         lwork[l] += static_cast<double>(J.nx) * J.ny * J.nz * J.k * (J.comp ? 10.0 : 1.0);
         for (int bz = 0; bz < J.chunks; ++bz)
             for (int by = 0; by < J.tiles_y; ++by)
@@ -299,7 +332,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     const size_t off_maps = ((njobs * sizeof(sep::Job)) + 127) & ~size_t(127);
     const size_t off_items = off_maps + njobs * sizeof(CUtensorMap);
     const size_t off_counter = off_items + std::max<size_t>(1, items.size()) * sizeof(int4);
-    const size_t total = off_counter + 2 * NKS * 128;   // counters 128 bytes apart
+    const size_t total = off_counter + 4 * NKS * 128;   // counters 128 bytes apart
     cudaError_t e = cudaMalloc(&P.dmem, total);
     if (e != cudaSuccess) return from_cuda(e);
     unsigned char* base = static_cast<unsigned char*>(P.dmem);
@@ -321,7 +354,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
     for (int l = 0; l < NL; ++l) {
         const int nl = loff[l + 1] - loff[l];
         if (nl == 0) continue;
-        BatchKernel kern = batch_kernel(KS[l / 2], l % 2 == 1);
+        BatchKernel kern = batch_kernel(KS[l / 4], (l / 2) % 2 == 1, l % 2 == 1);
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(lsmem[l]));
         if (e != cudaSuccess) return from_cuda(e);
@@ -376,7 +409,7 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
             if (nl == 0) continue;
             e = cudaStreamWaitEvent(side[l], fork, 0);
             if (e != cudaSuccess) break;
-            batch_kernel(KS[l / 2], l % 2 == 1)<<<lgrid[l], sep::NT, lsmem[l], side[l]>>>(
+            batch_kernel(KS[l / 4], (l / 2) % 2 == 1, l % 2 == 1)<<<lgrid[l], sep::NT, lsmem[l], side[l]>>>(
                 P.d_jobs, P.d_maps, P.d_items + loff[l], nl, P.d_counter + 32 * l, ctx.status);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(join[l], side[l]);
@@ -443,8 +476,9 @@ vktError build_plan(Plan& P, int32_t n, vktStructuredVolume* dst, vktStructuredV
                 per_sm_cap);
         for (int l = 0; l < NL; ++l)
             if (loff[l + 1] > loff[l])
-                fprintf(stderr, "[vkt]   k=%d%s: %d bricks, grid %d, smem %zu\n", KS[l / 2],
-                        l % 2 ? " compensated" : "", loff[l + 1] - loff[l], lgrid[l], lsmem[l]);
+                fprintf(stderr, "[vkt]   k=%d%s%s: %d bricks, grid %d, smem %zu\n", KS[l / 4],
+                        (l / 2) % 2 ? " compensated" : "", l % 2 ? " narrow" : "",
+                        loff[l + 1] - loff[l], lgrid[l], lsmem[l]);
     }
     return VKT_NO_ERROR;
 }
@@ -542,8 +576,10 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
         const bool force_dense = pol.path == VKT_PATH_DIRECT || pol.path == VKT_PATH_TENSOR;
         const bool force_direct = pol.path == VKT_PATH_DIRECT;
         cudaStream_t pstream = static_cast<cudaStream_t>(pol.stream);
-        // brick z extent and persistent grid: the tuned choice of this batch shape, else the
-        // rule (64-plane bricks, as many CTAs per SM as fit), else measured now
+        // brick z extent, brick shape and persistent grid: the tuned choice of this batch
+        // shape, else the rule (64-plane bricks, the narrow shape where it pads less, as many
+        // CTAs per SM as fit), else measured now.  A batch choice's `path` field holds the
+        // CTAs-per-SM cap in bits 0-3 and, in bit 4, that the narrow shape is not used.
         char tkey[96];
         std::snprintf(tkey, sizeof(tkey), "batch n%d %016llx", n,
                       static_cast<unsigned long long>(shape_hash));
@@ -557,38 +593,42 @@ extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, v
         if (measure) {
             // every candidate plan is built and replayed on the policy stream; the fastest
             // is kept (the replays write the destinations, as the call itself does)
-            const TuneChoice cand[5] = {{0, 64, 0.f}, {0, 32, 0.f}, {0, 128, 0.f}, {1, 64, 0.f},
-                                        {1, 32, 0.f}};
-            std::vector<Plan> plans(5);
-            for (int c = 0; c < 5 && err == VKT_NO_ERROR; ++c) {
+            constexpr int NC = 6;
+            const TuneChoice cand[NC] = {{0, 64, 0.f},  {0, 32, 0.f},  {0, 128, 0.f},
+                                         {1, 64, 0.f},  {16, 64, 0.f}, {16, 32, 0.f}};
+            std::vector<Plan> plans(NC);
+            for (int c = 0; c < NC && err == VKT_NO_ERROR; ++c) {
                 plans[c].key = key;
                 plans[c].device = dev;
                 err = build_plan(plans[c], n, dst, src, filters, sep_idx, dense_idx, force_dense,
-                                 force_direct, ctx, cand[c].zchunk, cand[c].path);
+                                 force_direct, ctx, cand[c].zchunk, cand[c].path & 15,
+                                 (cand[c].path & 16) == 0);
             }
             if (err == VKT_NO_ERROR) {
-                err = autotune_time(cand, 5, [&](const TuneChoice& t) {
+                err = autotune_time(cand, NC, [&](const TuneChoice& t) {
                     const int c = static_cast<int>(&t - cand);
                     count_launches(plans[c].kernels);
                     return from_cuda(cudaGraphLaunch(plans[c].exec, pstream));
                 }, pstream, &tc);
             }
             int keep = -1;
-            for (int c = 0; c < 5; ++c)
+            for (int c = 0; c < NC; ++c)
                 if (err == VKT_NO_ERROR && cand[c].zchunk == tc.zchunk && cand[c].path == tc.path) keep = c;
-            for (int c = 0; c < 5; ++c)
+            for (int c = 0; c < NC; ++c)
                 if (c != keep) plans[c].release();
             if (err != VKT_NO_ERROR || keep < 0) return err != VKT_NO_ERROR ? err : VKT_ERROR_CUDA;
             autotune_store(tkey, tc);
             if (ctx.debug & VKT_DEBUG_LOG)
-                fprintf(stderr, "[vkt] autotune %s: brick z target %d, CTAs per SM cap %d, %.4f ms\n",
-                        tkey, tc.zchunk, tc.path, tc.ms);
+                fprintf(stderr, "[vkt] autotune %s: brick z target %d, CTAs per SM cap %d, "
+                        "narrow bricks %s, %.4f ms\n", tkey, tc.zchunk, tc.path & 15,
+                        (tc.path & 16) ? "off" : "on", tc.ms);
             P = std::move(plans[keep]);
         } else {
             P.key = key;
             P.device = dev;
             err = build_plan(P, n, dst, src, filters, sep_idx, dense_idx, force_dense, force_direct,
-                             ctx, tc.zchunk > 0 ? tc.zchunk : 64, std::max(0, tc.path));
+                             ctx, tc.zchunk > 0 ? tc.zchunk : 64, std::max(0, tc.path) & 15,
+                             (std::max(0, tc.path) & 16) == 0);
             if (err != VKT_NO_ERROR) {
                 P.release();
                 return err;

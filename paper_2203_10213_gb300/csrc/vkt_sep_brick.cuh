@@ -22,6 +22,8 @@ constexpr int NT = 256;
 constexpr int BX = 16, BY = 16;
 constexpr int RX = 4, RY = 2;
 constexpr int TX = BX * RX, TY = BY * RY;
+constexpr int CRY = 1;              // output rows per thread of the compensated brick
+constexpr int CTY = BY * CRY;
 constexpr int STAGES = 4;    // barriers per CTA; planes in flight of the compensated brick
 constexpr int FSTAGES = 3;   // planes in flight of the float brick (measured faster than 4)
 // How a brick fills its stages, fixed at compile time where the caller knows it (the plane
@@ -90,21 +92,30 @@ __device__ __forceinline__ float byte_float(uint32_t w, int i)
     return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u + i)) - 8388608.f;
 }
 
-template <int K, int NS = FSTAGES>
+// the output tile of a brick with BXG threads along x (64 x 32 by default, 32 x 32 narrow)
+// and of its compensated twin (64 x 16, 32 x 32 narrow)
+template <int BXG>
+constexpr int tile_x() { return BXG * RX; }
+template <int BXG>
+constexpr int tile_y() { return (NT / BXG) * (BXG == BX ? RY : 1); }
+template <int BXG>
+constexpr int tile_y_comp() { return (NT / BXG) * CRY; }
+
+template <int K, int NS = FSTAGES, int BXG = BX>
 __host__ __device__ constexpr size_t smem_bytes_fx(int sfmt)
 {
-    using Geo = Brick<K, TX, TY>;
+    using Geo = Brick<K, tile_x<BXG>(), tile_y<BXG>()>;
     return 128 + static_cast<size_t>(NS) * Geo::stage_bytes(sfmt, false) +
-           2 * static_cast<size_t>(Geo::FH) * TX * sizeof(float);
+           2 * static_cast<size_t>(Geo::FH) * tile_x<BXG>() * sizeof(float);
 }
 
-template <int K, int NS = FSTAGES>
+template <int K, int NS = FSTAGES, int BXG = BX>
 __host__ __device__ constexpr size_t smem_bytes(int sfmt, bool rows = false)
 {
-    using Geo = Brick<K, TX, TY>;
+    using Geo = Brick<K, tile_x<BXG>(), tile_y<BXG>()>;
     return 128 + static_cast<size_t>(NS) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +      // float tile
-           static_cast<size_t>(Geo::FH) * TX * sizeof(float);            // x-pass output
+           static_cast<size_t>(Geo::FH) * tile_x<BXG>() * sizeof(float);  // x-pass output
 }
 
 // Initialises the stage barriers (thread 0; the caller synchronises afterwards).
@@ -134,12 +145,17 @@ __device__ __forceinline__ void init_barriers(unsigned char* smem)
 // arithmetic.  A persistent CTA (the batch) carries gplane from brick to brick and must use
 // the general ring, whatever NS and K are.
 template <int K, class Wt, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false,
-          int NS = FSTAGES, bool STATIC = false, bool ROTZ = false>
+          int NS = FSTAGES, bool STATIC = false, bool ROTZ = false, int BXG = BX>
 __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorMap* tmap, int bx,
                                       int by, int bz, unsigned char* smem, uint32_t& gplane,
                                       unsigned* status)
 {
     static_assert(!STATIC || NS == K, "the static ring has one stage per unrolled plane");
+    // the brick's shape (shadowing the namespace's defaults): BXG threads along x, four
+    // outputs each; the narrow shape (BXG = 8) has 32 x 32 outputs, one row per thread
+    constexpr int BX = BXG, BY = NT / BXG;
+    constexpr int RY = BXG == sep::BX ? sep::RY : 1;
+    constexpr int TX = BX * RX, TY = BY * RY;
     using Geo = Brick<K, TX, TY>;
     constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
     constexpr int XGROUPS = TX / 4;
@@ -497,23 +513,24 @@ __device__ __forceinline__ bool brick(const Job& J, const Wt& G, const CUtensorM
 // the pair.  One output row per thread (RY = 1) keeps the 2 x k x 4 accumulators in
 // registers.
 
-constexpr int CRY = 1;
-constexpr int CTY = BY * CRY;
 
-template <int K>
+template <int K, int BXG = BX>
 __host__ __device__ constexpr size_t smem_bytes_comp(int sfmt, bool rows = false)
 {
-    using Geo = Brick<K, TX, CTY>;
+    using Geo = Brick<K, tile_x<BXG>(), tile_y_comp<BXG>()>;
     return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +
-           static_cast<size_t>(Geo::FH) * TX * sizeof(float2);           // (hi, lo) x pass
+           static_cast<size_t>(Geo::FH) * tile_x<BXG>() * sizeof(float2);  // (hi, lo) x pass
 }
 
-template <int K, class Wt, int LM = LM_ANY, bool ROI = false>
+template <int K, class Wt, int LM = LM_ANY, bool ROI = false, int BXG = BX>
 __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUtensorMap* tmap,
                                            int bx, int by, int bz, unsigned char* smem,
                                            uint32_t& gplane, unsigned* status)
 {
+    // the brick's shape (shadowing the namespace's defaults): BXG threads along x
+    constexpr int BX = BXG, BY = NT / BXG;
+    constexpr int TX = BX * RX, CTY = BY * CRY;
     using Geo = Brick<K, TX, CTY>;
     constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
     constexpr int XGROUPS = TX / 4;

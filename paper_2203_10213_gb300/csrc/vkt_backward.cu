@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(NT)
 {
     using Geo = Brick<K, TX, TY>;
     constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
+    __builtin_assume(threadIdx.x < NT);   // every launch has NT threads
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     constexpr int rawb = Geo::raw_bytes(FMT_F32);

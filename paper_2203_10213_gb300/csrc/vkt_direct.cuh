@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
     static_assert(!(COMP && ADJ), "the adjoint writes float32");
-    __builtin_assume(threadIdx.x < NT);   // every launch has NT threads
     using Cfg = DirectCfg<K, COMP>;
     using Geo = typename Cfg::Geo;
     constexpr int R = Geo::R, RX = Cfg::RX, RY = Cfg::RY;

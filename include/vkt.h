@@ -113,8 +113,10 @@ VKT_API vktError vktGetThreadExecutionPolicy(vktExecutionPolicy* policy);
  * extent rounded up to powers of two per axis -- times its candidates on the policy stream
  * (the rule's path, for dense filters that the tensor path can evaluate also the other
  * path, and three brick z extents of the CUDA-core paths), keeps the fastest and uses it
- * from then on.  That first call synchronises the policy stream and launches each candidate
- * four times into the destination (then the chosen one once more); a call made while
+ * from then on (the rule's choice unless another is more than 2 % faster).  That first call
+ * synchronises the policy stream and launches each candidate eight times into the destination
+ * (two interleaved passes of one untimed and three timed launches; then the chosen one once
+ * more); a call made while
  * its stream is being captured into a graph uses the rule.  vktApplyFilterBatchSV tunes
  * each new batch plan the same way (brick z extent, persistent grid).  The choices live in
  * memory; when VKT_AUTOTUNE_CACHE names a file they are read from it at the first lookup and

@@ -778,18 +778,22 @@ static vktError apply_filter(vktStructuredVolume dst, vktStructuredVolume src, v
                 zchunk = std::max(0, c.zchunk);
             }
         } else if (!stream_capturing(ctx.stream)) {
+            // candidate 0 is the rule (its path, the launcher's z chunks); the tuner keeps
+            // it unless another candidate is clearly faster
             TuneChoice cand[8];
             int n = 0;
+            cand[n].path = path;
+            cand[n++].zchunk = 0;
             const int ez = ext[2];
-            const int zs[3] = {0, std::max(1, (ez + 15) / 16), std::max(1, (ez + 3) / 4)};
+            const int zs[2] = {std::max(1, (ez + 15) / 16), std::max(1, (ez + 3) / 4)};
             const int cpath = filter->separable ? VKT_PATH_SEPARABLE : VKT_PATH_DIRECT;
-            for (int i = 0; i < 3; ++i) {
+            for (int i = 0; i < 2; ++i) {
                 if (i > 0 && zs[i] == zs[i - 1]) continue;
                 cand[n].path = cpath;
                 cand[n++].zchunk = zs[i];
             }
-            if (!filter->separable && tensor_ok) {
-                cand[n].path = VKT_PATH_TENSOR;
+            if (path == VKT_PATH_TENSOR) {   // the other path at its rule's z chunks
+                cand[n].path = cpath;
                 cand[n++].zchunk = 0;
             }
             err = autotune_time(cand, n, [&](const TuneChoice& t) { return launch(t.path, t.zchunk); },

@@ -228,9 +228,19 @@ def cpu_leg(args, vol, pin):
     states the error of each GPU path."""
     import oracle
     rate, n, dt = oracle_sample_rate(vol, args.cpu_seconds)
-    cpu = {"value": round(rate / 1e9, 6), "unit": "Gvoxel/s", "cores": oracle.num_threads(),
+    cores = oracle.num_threads()
+    cpu = {"value": round(rate / 1e9, 6), "unit": "Gvoxel/s", "cores": cores,
            "kind": "oracle",
            "sample": f"{n} random voxels of the 512^3 volume, both filters, FP64 C, {dt:.1f} s"}
+    # one core on a shorter sample; the whole step's time extrapolated from its rate
+    oracle.set_num_threads(1)
+    try:
+        rate1, n1, dt1 = oracle_sample_rate(vol, max(1.0, args.cpu_seconds / 5))
+    finally:
+        oracle.set_num_threads(cores)
+    cpu["single_core"] = {"value": round(rate1 / 1e9, 6), "unit": "Gvoxel/s",
+                          "sample": f"{n1} random voxels, {dt1:.1f} s, one thread",
+                          "step_s_extrapolated": round(2 * float(vol.size) / rate1, 1)}
     refs = None
     if pin is not None:
         field, idx, kernels = pin

@@ -76,6 +76,8 @@ def _load():
             lib.oracle_backward_input_points.restype = i32
             lib.oracle_backward_input_points.argtypes = [p, i64, i64, i64, p, i32, p, i64, p]
             lib.oracle_num_threads.restype = i32
+            lib.oracle_set_num_threads.restype = None
+            lib.oracle_set_num_threads.argtypes = [i32]
             lib.oracle_render.restype = i32
             lib.oracle_render.argtypes = [p, i32, d, d, i64, i64, i64, i32, i32, p, p, p, d, d, d,
                                           p, i32, p, p]
@@ -108,6 +110,11 @@ def _fmt_of(vol: np.ndarray) -> int:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (timing only; results do not depend on it)."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def dense_weights(w) -> np.ndarray:

@@ -284,6 +284,18 @@ int oracle_num_threads(void)
 #endif
 }
 
+/* Threads of the parallel loops over output voxels (timing only; results do not depend on
+ * it: every voxel's sum is evaluated by one thread in the definition's tap order). */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
 /*
  * CLAHE-3D (Sec. 4.1 "Case Study: CLAHE-3D": contrast limited adaptive histogram
  * equalisation, a 3-D variant of the 2-D method; brick decomposition, local histograms, a

@@ -398,6 +398,7 @@ vktError launch_wg_noalloc(const float* x, const float* gy, int nx, int ny, int 
 extern "C" vktError vktApplyFilterWeightGradNoAllocSV(float* gradWeights, vktStructuredVolume gradDst,
                                                       vktStructuredVolume src, vktFilter filter)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterWeightGradNoAllocSV");
     if (!gradDst || gradDst->magic != VKT_VOLUME_MAGIC || !src || src->magic != VKT_VOLUME_MAGIC ||
         !filter || filter->magic != VKT_FILTER_MAGIC)
         return VKT_ERROR_INVALID_HANDLE;

@@ -491,6 +491,7 @@ using namespace vkt;
 extern "C" vktError vktApplyFilterBatchSV(int32_t n, vktStructuredVolume* dst, vktStructuredVolume* src,
                                           vktFilter* filters)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterBatchSV");
     if (n < 1 || !dst || !src || !filters) return VKT_ERROR_INVALID_VALUE;
     for (int i = 0; i < n; ++i) {
         if (!valid_volume(dst[i]) || !valid_volume(src[i]) || !valid_filter(filters[i]))

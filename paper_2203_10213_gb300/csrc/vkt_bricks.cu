@@ -428,6 +428,7 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
                              vktStructuredVolume volume, int32_t brickX, int32_t brickY,
                              int32_t brickZ, int32_t ghost)
 {
+    vkt::CallRange nvtx_range("vktBrickDecomposeSV");
     if (!valid_volume(volume)) return VKT_ERROR_INVALID_HANDLE;
     if (!bricks || brickX < 1 || brickY < 1 || brickZ < 1 || ghost < 0)
         return VKT_ERROR_INVALID_VALUE;

@@ -315,6 +315,7 @@ using namespace vkt;
 extern "C" vktError vktClahe3DSV(vktStructuredVolume dst, vktStructuredVolume src, int32_t bricksX,
                                  int32_t bricksY, int32_t bricksZ, float clipLimit)
 {
+    vkt::CallRange nvtx_range("vktClahe3DSV");
     if (!valid_volume(dst) || !valid_volume(src)) return VKT_ERROR_INVALID_HANDLE;
     if (dst->dims[0] != src->dims[0] || dst->dims[1] != src->dims[1] || dst->dims[2] != src->dims[2])
         return VKT_ERROR_DIMS_MISMATCH;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "vkt.h"
@@ -28,6 +29,16 @@ struct vktFilter_impl {
 };
 
 namespace vkt {
+
+// An NVTX range named after a public call, open for the call's host-side duration (a
+// profiler's timeline shows each call and the launches it enqueues; without a tool attached
+// the push and pop return at once).
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
 
 // One filter application as the kernels see it.
 struct Job {

@@ -149,6 +149,7 @@ using namespace vkt;
 extern "C" vktError vktRenderSV(float* rgba, int32_t width, int32_t height, vktStructuredVolume volume,
                                 const vktRenderParams* params)
 {
+    vkt::CallRange nvtx_range("vktRenderSV");
     if (!valid_volume(volume)) return VKT_ERROR_INVALID_HANDLE;
     if (!rgba || !params || width < 1 || height < 1 || height > 65535 * BY) return VKT_ERROR_INVALID_VALUE;
     const vktRenderParams& p = *params;

@@ -914,6 +914,7 @@ static vktError check_filter_args(vktStructuredVolume dst, vktStructuredVolume s
 
 vktError vktApplyFilterSV(vktStructuredVolume dst, vktStructuredVolume src, vktFilter filter)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterSV");
     const vktError err = check_filter_args(dst, src, filter);
     if (err != VKT_NO_ERROR) return err;
     return apply_filter(dst, src, filter, nullptr);
@@ -923,6 +924,7 @@ vktError vktApplyFilterRangeSV(vktStructuredVolume dst, vktStructuredVolume src,
                                vktFilter filter, int32_t firstX, int32_t firstY, int32_t firstZ,
                                int32_t lastX, int32_t lastY, int32_t lastZ)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterRangeSV");
     const vktError err = check_filter_args(dst, src, filter);
     if (err != VKT_NO_ERROR) return err;
     const int32_t box[6] = {firstX, firstY, firstZ, lastX, lastY, lastZ};
@@ -941,6 +943,7 @@ vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeight
                                   vktStructuredVolume gradDst, vktStructuredVolume src,
                                   vktFilter filter)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterBackwardSV");
     if (!valid(gradDst) || !valid(src) || !valid(filter)) return VKT_ERROR_INVALID_HANDLE;
     if (gradSrc && !valid(gradSrc)) return VKT_ERROR_INVALID_HANDLE;
     if (src->format != vktDataFormatFloat32 || gradDst->format != vktDataFormatFloat32 ||
@@ -1024,6 +1027,7 @@ vktError vktApplyFilterBackwardBatchSV(int32_t n, vktStructuredVolume* gradSrcs,
                                        vktStructuredVolume* gradDsts, vktStructuredVolume* srcs,
                                        vktFilter filter)
 {
+    vkt::CallRange nvtx_range("vktApplyFilterBackwardBatchSV");
     if (n < 1 || !gradDsts || !srcs) return VKT_ERROR_INVALID_VALUE;
     if (!valid(filter)) return VKT_ERROR_INVALID_HANDLE;
     for (int32_t b = 0; b < n; ++b) {

@@ -98,15 +98,8 @@ __global__ void __launch_bounds__(NT)
         for (int a = 0; a < K; ++a) acc[b][a] = 0.f;
 
     const int ox = x0 + tx * RX;
-    bool failed = false;
-    for (int it = 0; it < nplanes; ++it) {
-        const int s = it % STAGES;
-        const int z = zc0 + it;
-        const unsigned char* rs = raw + s * rawb;
-        float* Fb = F + (it & 1) * FH * FP;
-        bool ok = true;
-        // gy block of this thread (zero outside the volume so it adds nothing)
-        float g[RY][RX];
+    // gy block of this thread in plane z (zero outside the volume so it adds nothing)
+    auto load_g = [&](int z, float (&g)[RY][RX]) {
 #pragma unroll
         for (int i = 0; i < RY; ++i) {
             const int oy = y0 + ty * RY + i;
@@ -115,6 +108,18 @@ __global__ void __launch_bounds__(NT)
             for (int x = 0; x < RX; ++x)
                 g[i][x] = (oy < p.ny && ox + x < p.nx) ? __ldg(gyv + row + ox + x) : 0.f;
         }
+    };
+    // the block of the next plane is loaded before the FMAs of this one (its latency hides
+    // behind them)
+    float g[RY][RX];
+    if (nplanes > 0) load_g(zc0, g);
+    bool failed = false;
+    for (int it = 0; it < nplanes; ++it) {
+        const int s = it % STAGES;
+        const int z = zc0 + it;
+        const unsigned char* rs = raw + s * rawb;
+        float* Fb = F + (it & 1) * FH * FP;
+        bool ok = true;
         if (p.use_tma) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
         } else {
@@ -133,6 +138,8 @@ __global__ void __launch_bounds__(NT)
                         clampi(zc0 + it + STAGES + c - R, 0, p.nz - 1), vol);
             ++issued;
         }
+        float gn[RY][RX];
+        if (it + 1 < nplanes) load_g(z + 1, gn);
 #pragma unroll
         for (int j = 0; j < RY + K - 1; ++j) {
             float win[RX + K - 1];
@@ -146,6 +153,12 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                     for (int x = 0; x < RX; ++x) acc[b][a] = fmaf(g[i][x], win[x + a], acc[b][a]);
             }
+        }
+        if (it + 1 < nplanes) {
+#pragma unroll
+            for (int i = 0; i < RY; ++i)
+#pragma unroll
+                for (int x = 0; x < RX; ++x) g[i][x] = gn[i][x];
         }
     }
     if (failed) {

@@ -22,9 +22,12 @@
 // a plain correlation of x_ext, so its adjoint is E^T applied to the zero-padded correlation
 // of gy with the flipped kernel, Z(j') = sum_d w[-d] gy0(j' + d) for j' in [-r, n+r)^3.
 // E^T folds Z onto the volume: gx(j) = sum of Z(j') over the j' whose clamp is j.  The
-// kernel computes Z brick by brick (TMA zero-fills positions outside gy), stores Z
-// directly where j' is strictly inside the volume (exactly one contribution) and
-// atomically adds it to the face voxel clamp(j') everywhere else.
+// kernel computes Z on the volume itself, j' in [0, n)^3 (TMA zero-fills gy outside), where
+// each Z(j') is the one contribution that lands on j' from inside, and stores it; the shell
+// of positions outside the volume, j' in [-r, n+r)^3 \ [0, n)^3, is then evaluated point by
+// point by k_adjoint_shell and added atomically to the face voxels it folds onto.  (A kernel
+// over the padded domain itself needed 3 x 5 column tiles instead of 2 x 4 at 128^3, and
+// atomics wherever a position folds: twice the forward's time.)
 //
 // Compensated mode (COMP, integer destinations whose FP32 error bound could flip a code):
 // every tap is added as an error-free product and sum (dot2_exact, the compensated dot
@@ -88,27 +91,6 @@ __host__ __device__ constexpr size_t direct_smem_bytes(int sfmt, bool rows)
     using Geo = typename DirectCfg<K, COMP>::Geo;
     return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
-}
-
-// Adjoint store of one row of Z values at padded-domain positions (oz, oy, ox + x).
-template <int RX>
-__device__ __forceinline__ void store_row_adjoint(float* dst, int nx, int ny, int nz, int R, int oz,
-                                                  int oy, int ox, const float (&z)[RX])
-{
-    if (oy < -R || oy >= ny + R || oz < -R || oz >= nz + R) return;
-    const int cy = clampi(oy, 0, ny - 1), cz = clampi(oz, 0, nz - 1);
-    const bool inner_yz = oy > 0 && oy < ny - 1 && oz > 0 && oz < nz - 1;
-    const int64_t rowbase = (static_cast<int64_t>(cz) * ny + cy) * nx;
-#pragma unroll
-    for (int x = 0; x < RX; ++x) {
-        const int xx = ox + x;
-        if (xx < -R || xx >= nx + R) continue;
-        const int cx = clampi(xx, 0, nx - 1);
-        if (inner_yz && xx > 0 && xx < nx - 1)
-            dst[rowbase + cx] = z[x];
-        else
-            atomicAdd(dst + rowbase + cx, z[x]);
-    }
 }
 
 // SF/DF: source and destination formats fixed at compile time (-1: read from the arguments);
@@ -388,10 +370,7 @@ __global__ void __launch_bounds__(NT)
                 float row[RX];
 #pragma unroll
                 for (int x = 0; x < RX; ++x) row[x] = lane(sl0, i, x);
-                if (ADJ) {
-                    store_row_adjoint<RX>(static_cast<float*>(dst), p.nx, p.ny, p.nz, R, oz, oy,
-                                          ox, row);
-                } else if (oy < yend && nvalid > 0) {
+                if (oy < yend && nvalid > 0) {
                     const int64_t idx = (static_cast<int64_t>(oz) * p.ny + oy) * p.nx + ox;
                     store_row<RX>(dst, dfmt, idx, nvalid, row, p.a0, p.a1, p.qmax, first);
                 }
@@ -437,6 +416,66 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
+// The adjoint's shell: Z(j') = sum_d w[-d] gy0(j' + d) at the positions j' of [-r, n+r)^3
+// outside [0, n)^3 (W holds the flipped weights, gy0 is zero outside the volume), each added
+// atomically to gx(clamp(j')), the face voxel it folds onto.  One thread per position,
+// blockIdx.y the volume of the batch; the shell is enumerated as the z slabs (z outside the
+// volume), then the y slabs of the planes inside, then the x slabs of the rows inside.
+template <int K>
+__global__ void __launch_bounds__(256)
+    k_adjoint_shell(const float* __restrict__ gy, float* gx, int nx, int ny, int nz,
+                    int64_t vs_src, int64_t vs_dst, const DenseW<K> W)
+{
+    constexpr int R = (K - 1) / 2;
+    const float* g = gy + static_cast<int64_t>(blockIdx.y) * vs_src;
+    float* out = gx + static_cast<int64_t>(blockIdx.y) * vs_dst;
+    const int64_t px = nx + 2 * R, py = ny + 2 * R;
+    const int64_t na = 2LL * R * py * px, nb = 2LL * R * nz * px, nc = 2LL * R * nz * ny;
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= na + nb + nc) return;
+    int x, y, z;
+    if (i < na) {
+        const int64_t zz = i / (py * px), rem = i - zz * py * px;
+        z = zz < R ? static_cast<int>(zz) - R : nz + static_cast<int>(zz) - R;
+        y = static_cast<int>(rem / px) - R;
+        x = static_cast<int>(rem % px) - R;
+    } else if (i < na + nb) {
+        const int64_t j = i - na, per = 2LL * R * px;
+        z = static_cast<int>(j / per);
+        const int64_t rem = j - z * per;
+        const int yy = static_cast<int>(rem / px);
+        y = yy < R ? yy - R : ny + yy - R;
+        x = static_cast<int>(rem % px) - R;
+    } else {
+        const int64_t j = i - na - nb, per = 2LL * R * ny;
+        z = static_cast<int>(j / per);
+        const int64_t rem = j - z * per;
+        y = static_cast<int>(rem / (2 * R));
+        const int xx = static_cast<int>(rem % (2 * R));
+        x = xx < R ? xx - R : nx + xx - R;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        const int zz = z + c - R;
+        if (zz < 0 || zz >= nz) continue;
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const int yy = y + b - R;
+            if (yy < 0 || yy >= ny) continue;
+            const float* row = g + (static_cast<int64_t>(zz) * ny + yy) * nx;
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+                const int xx = x + a - R;
+                if (xx >= 0 && xx < nx) acc = fmaf(W.w[(c * K + b) * K + a], __ldg(row + xx), acc);
+            }
+        }
+    }
+    const int64_t idx = (static_cast<int64_t>(clampi(z, 0, nz - 1)) * ny + clampi(y, 0, ny - 1)) * nx +
+                        clampi(x, 0, nx - 1);
+    atomicAdd(out + idx, acc);
+}
+
 // One launch of the direct kernel over the job's region (forward) or over the padded
 // domain (adjoint); COMP: compensated accumulation into an integer destination.
 template <int K, bool ADJ, bool COMP = false>
@@ -462,14 +501,11 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     a.status = ctx.status;
     a.withhold_first = (ctx.debug & VKT_DEBUG_INJECT_WAIT_TIMEOUT) ? 1 : 0;
     if (ADJ) {
-        // padded output domain [-r, n+r) per axis; x starts 16 bytes left of the domain
-        // so that every tile's TMA box starts on a 16-byte boundary
-        a.ox0 = -fmt_xalign(job.sfmt);
-        a.oy0 = -R;
-        a.oz0 = -R;
-        a.ex = job.nx + R - a.ox0;
-        a.ey = job.ny + 2 * R;
-        a.ez = job.nz + 2 * R;
+        // Z on the volume's own positions (the shell outside it: k_adjoint_shell)
+        a.ox0 = a.oy0 = a.oz0 = 0;
+        a.ex = job.nx;
+        a.ey = job.ny;
+        a.ez = job.nz;
         a.sx0 = 0;
         a.sx1 = job.nx;
         a.sy1 = job.ny;
@@ -570,6 +606,18 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return from_cuda(e);
+        if constexpr (ADJ && R > 0) {
+            // the shell outside the volumes, folded onto their faces after the main launch
+            const int64_t shell = 2LL * R *
+                                  ((job.ny + 2LL * R) * (job.nx + 2LL * R) + static_cast<int64_t>(job.nz) *
+                                   (job.nx + 2LL * R) + static_cast<int64_t>(job.nz) * job.ny);
+            k_adjoint_shell<K><<<dim3(static_cast<unsigned>((shell + 255) / 256), nv), 256, 0, ctx.stream>>>(
+                static_cast<const float*>(a.src), static_cast<float*>(a.dst), job.nx, job.ny, job.nz,
+                a0.vs_src, a0.vs_dst, W);
+            count_launches(1);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return from_cuda(e);
+        }
     }
     return VKT_NO_ERROR;
 }

@@ -114,8 +114,9 @@ struct Ctx {
 // the compensated kernels when job.comp is set (launch_direct_comp).
 vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx);
 vktError launch_direct_comp(const Job& job, const float* w, int k, const Ctx& ctx);
-// dL/dsrc of the clamped correlation (float32 gy in job.src, gx in job.dst; gx must be
-// zeroed first: face voxels are accumulated atomically).
+// dL/dsrc of the clamped correlation (float32 gy in job.src, gx in job.dst): every voxel of
+// gx is written (the main launch), then the shell outside the volume is added to the face
+// voxels (a second, small launch).
 vktError launch_adjoint(const Job& job, const float* w, int k, const Ctx& ctx);
 // dL/dw summed over nvol volumes of equal dims (volume v of x at x + v vs_x, of gy at
 // gy + v vs_gy): per-CTA FP32 partial sums into `partials` (capacity `cap` floats), then

@@ -962,9 +962,7 @@ vktError vktApplyFilterBackwardSV(vktStructuredVolume gradSrc, float* gradWeight
     const int k = filter->k;
     const int nx = src->dims[0], ny = src->dims[1], nz = src->dims[2];
     if (gradSrc) {
-        // face voxels of dL/dsrc are accumulated atomically: start from zero
-        cudaError_t e = cudaMemsetAsync(gradSrc->data, 0, volume_bytes(gradSrc), ctx.stream);
-        if (e != cudaSuccess) return from_cuda(e);
+        // the adjoint writes every voxel, then adds the shell outside the volume to the faces
         Job job{};
         job.src = gradDst->data;
         job.dst = gradSrc->data;
@@ -1054,13 +1052,7 @@ vktError vktApplyFilterBackwardBatchSV(int32_t n, vktStructuredVolume* gradSrcs,
     const bool even_gy = evenly_spaced(n, gradDsts, &s_gy);
     const bool even_gx = gradSrcs && evenly_spaced(n, gradSrcs, &s_gx);
     if (gradSrcs) {
-        // face voxels of dL/dsrc are accumulated atomically: start from zero
-        const uint64_t vb = volume_bytes(gradSrcs[0]);
-        const bool packed = even_gx && (n == 1 || static_cast<uint64_t>(s_gx) * 4 == vb);
-        for (int32_t b = 0; b < (packed ? 1 : n); ++b) {
-            cudaError_t e = cudaMemsetAsync(gradSrcs[b]->data, 0, packed ? vb * n : vb, ctx.stream);
-            if (e != cudaSuccess) return from_cuda(e);
-        }
+        // the adjoint writes every voxel, then adds the shell outside the volume to the faces
         Job job{};
         job.nx = nx;
         job.ny = ny;

@@ -24,8 +24,8 @@
 // E^T folds Z onto the volume: gx(j) = sum of Z(j') over the j' whose clamp is j.  The
 // kernel computes Z on the volume itself, j' in [0, n)^3 (TMA zero-fills gy outside), where
 // each Z(j') is the one contribution that lands on j' from inside, and stores it; the shell
-// of positions outside the volume, j' in [-r, n+r)^3 \ [0, n)^3, is then evaluated point by
-// point by k_adjoint_shell and added atomically to the face voxels it folds onto.  (A kernel
+// of positions outside the volume, j' in [-r, n+r)^3 \ [0, n)^3, is then folded slab by slab
+// by k_adjoint_shell and added atomically to the face voxels it lands on.  (A kernel
 // over the padded domain itself needed 3 x 5 column tiles instead of 2 x 4 at 128^3, and
 // atomics wherever a position folds: twice the forward's time.)
 //
@@ -416,64 +416,125 @@ __global__ void __launch_bounds__(NT)
     }
 }
 
-// The adjoint's shell: Z(j') = sum_d w[-d] gy0(j' + d) at the positions j' of [-r, n+r)^3
-// outside [0, n)^3 (W holds the flipped weights, gy0 is zero outside the volume), each added
-// atomically to gx(clamp(j')), the face voxel it folds onto.  One thread per position,
-// blockIdx.y the volume of the batch; the shell is enumerated as the z slabs (z outside the
-// volume), then the y slabs of the planes inside, then the x slabs of the rows inside.
+// The adjoint's shell: the positions j' of [-r, n+r)^3 outside [0, n)^3, each of whose
+// Z(j') = sum_d w[-d] gy0(j' + d) (W holds the flipped weights, gy0 is zero outside the
+// volume) is added to gx(clamp(j')).  The shell is taken as three pairs of slabs: z outside
+// the volume (x', y' anywhere in the padded range), then z inside and y outside, then z and
+// y inside and x outside.  A slab folds along its own axis in one sum: for the low z face,
+// sum over z' in [-r, 0) of Z(x', y', z') = sum over planes zz in [0, r) and taps (b, a) of
+// Fz[zz][b][a] gy0(x' + a - r, y' + b - r, zz), with Fz[zz] = sum over c in [zz + r + 1, 2r]
+// of W[c] (the taps of W that reach plane zz from below the volume); for the high face the
+// planes are n - r + t, t in [0, r), with Fz[t] = sum over c in [0, t] of W[c]; likewise
+// along y and x.  Each folded slab is a thin 2-D correlation: out(p, q) = sum over t < r and
+// (u, v) in [0, k)^2 of F[t][u][v] S[t][p + u][q + v], S the r layers of gy next to the face.
+// A CTA takes a 16 x 16 tile of one slab's outputs, stages its S (with halo, zero outside
+// the volume) in shared memory, and adds each output atomically onto the face voxel it folds
+// onto; blockIdx.x enumerates the tiles of the six slabs, blockIdx.y the volume of the batch.
+// (One thread per shell position with k^3 taps read from global memory took 40 % of dL/dx at
+// 8 x 128^3, k = 5: the x slabs' loads hit a different row in every lane.)
+constexpr int SHELL_T = 16;   // output tile edge of the shell kernel (256 threads)
+
 template <int K>
-__global__ void __launch_bounds__(256)
+__host__ __device__ constexpr int shell_tiles(int nx, int ny, int nz, int* na, int* nb)
+{
+    constexpr int R = (K - 1) / 2, T = SHELL_T;
+    const int px = nx + 2 * R, py = ny + 2 * R;
+    const int a = 2 * ((py + T - 1) / T) * ((px + T - 1) / T);
+    const int b2 = 2 * ((nz + T - 1) / T) * ((px + T - 1) / T);
+    const int c = 2 * ((nz + T - 1) / T) * ((ny + T - 1) / T);
+    if (na) *na = a;
+    if (nb) *nb = b2;
+    return a + b2 + c;
+}
+
+template <int K>
+__global__ void __launch_bounds__(SHELL_T * SHELL_T)
     k_adjoint_shell(const float* __restrict__ gy, float* gx, int nx, int ny, int nz,
                     int64_t vs_src, int64_t vs_dst, const DenseW<K> W)
 {
-    constexpr int R = (K - 1) / 2;
+    constexpr int R = (K - 1) / 2, KK = K * K, RKK = R * K * K, T = SHELL_T, SP = T + 2 * R;
+    // folded weights [face: low, high][axis: z, y, x][t][u][v]: t the layer of the folded
+    // axis, (u, v) the other two taps in (c, b, a) order
+    __shared__ float fw[2][3][RKK];
+    __shared__ float S[R][SP][SP];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 6 * RKK; e += T * T) {
+        const int face = e / (3 * RKK), axis = (e / RKK) % 3, q = e % RKK;
+        const int t = q / KK, u = (q / K) % K, v = q % K;
+        const int f0 = face == 0 ? t + R + 1 : 0, f1 = face == 0 ? 2 * R : t;
+        float sum = 0.f;
+        for (int f = f0; f <= f1; ++f) {
+            const int c = axis == 0 ? f : u;
+            const int b = axis == 0 ? u : (axis == 1 ? f : v);
+            const int a = axis == 2 ? f : v;
+            sum += W.w[(c * K + b) * K + a];
+        }
+        fw[face][axis][q] = sum;
+    }
+    // this CTA's slab (0: z, 1: y, 2: x), face and tile
+    int na = 0, nb = 0;
+    shell_tiles<K>(nx, ny, nz, &na, &nb);
+    const int px = nx + 2 * R, py = ny + 2 * R;
+    int blk = blockIdx.x, slab, P, Q, offP, offQ;
+    if (blk < na) {
+        slab = 0; P = py; Q = px; offP = 2 * R; offQ = 2 * R;
+    } else if (blk < na + nb) {
+        blk -= na; slab = 1; P = nz; Q = px; offP = R; offQ = 2 * R;
+    } else {
+        blk -= na + nb; slab = 2; P = nz; Q = ny; offP = R; offQ = R;
+    }
+    const int tq = (Q + T - 1) / T, tp = (P + T - 1) / T;
+    const int face = blk / (tp * tq);
+    const int p0 = (blk / tq) % tp * T, q0 = blk % tq * T;
     const float* g = gy + static_cast<int64_t>(blockIdx.y) * vs_src;
     float* out = gx + static_cast<int64_t>(blockIdx.y) * vs_dst;
-    const int64_t px = nx + 2 * R, py = ny + 2 * R;
-    const int64_t na = 2LL * R * py * px, nb = 2LL * R * nz * px, nc = 2LL * R * nz * ny;
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= na + nb + nc) return;
-    int x, y, z;
-    if (i < na) {
-        const int64_t zz = i / (py * px), rem = i - zz * py * px;
-        z = zz < R ? static_cast<int>(zz) - R : nz + static_cast<int>(zz) - R;
-        y = static_cast<int>(rem / px) - R;
-        x = static_cast<int>(rem % px) - R;
-    } else if (i < na + nb) {
-        const int64_t j = i - na, per = 2LL * R * px;
-        z = static_cast<int>(j / per);
-        const int64_t rem = j - z * per;
-        const int yy = static_cast<int>(rem / px);
-        y = yy < R ? yy - R : ny + yy - R;
-        x = static_cast<int>(rem % px) - R;
-    } else {
-        const int64_t j = i - na - nb, per = 2LL * R * ny;
-        z = static_cast<int>(j / per);
-        const int64_t rem = j - z * per;
-        y = static_cast<int>(rem / (2 * R));
-        const int xx = static_cast<int>(rem % (2 * R));
-        x = xx < R ? xx - R : nx + xx - R;
+    // stage S[t][pp][qq] = gy0 at layer t of the face, p-axis p0 + pp - offP, q-axis
+    // q0 + qq - offQ (x slabs: the layer index fastest, the r voxels of a row are adjacent)
+    for (int e = tid; e < R * SP * SP; e += T * T) {
+        int t, pp, qq;
+        if (slab == 2) {
+            t = e % R;
+            qq = (e / R) % SP;
+            pp = e / (R * SP);
+        } else {
+            qq = e % SP;
+            pp = (e / SP) % SP;
+            t = e / (SP * SP);
+        }
+        const int pi = p0 + pp - offP, qi = q0 + qq - offQ;
+        int x, y, z;
+        if (slab == 0) {
+            x = qi; y = pi; z = face == 0 ? t : nz - R + t;
+        } else if (slab == 1) {
+            x = qi; y = face == 0 ? t : ny - R + t; z = pi;
+        } else {
+            x = face == 0 ? t : nx - R + t; y = qi; z = pi;
+        }
+        S[t][pp][qq] = (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz)
+                           ? __ldg(g + (static_cast<int64_t>(z) * ny + y) * nx + x)
+                           : 0.f;
     }
+    __syncthreads();
+    const int tx = tid % T, ty = tid / T;
+    const int p = p0 + ty, q = q0 + tx;
+    if (p >= P || q >= Q) return;
+    const float* f = fw[face][slab];
     float acc = 0.f;
 #pragma unroll
-    for (int c = 0; c < K; ++c) {
-        const int zz = z + c - R;
-        if (zz < 0 || zz >= nz) continue;
+    for (int t = 0; t < R; ++t)
 #pragma unroll
-        for (int b = 0; b < K; ++b) {
-            const int yy = y + b - R;
-            if (yy < 0 || yy >= ny) continue;
-            const float* row = g + (static_cast<int64_t>(zz) * ny + yy) * nx;
+        for (int u = 0; u < K; ++u)
 #pragma unroll
-            for (int a = 0; a < K; ++a) {
-                const int xx = x + a - R;
-                if (xx >= 0 && xx < nx) acc = fmaf(W.w[(c * K + b) * K + a], __ldg(row + xx), acc);
-            }
-        }
+            for (int v = 0; v < K; ++v) acc = fmaf(f[(t * K + u) * K + v], S[t][ty + u][tx + v], acc);
+    int ox, oy, oz;
+    if (slab == 0) {
+        ox = clampi(q - R, 0, nx - 1); oy = clampi(p - R, 0, ny - 1); oz = face == 0 ? 0 : nz - 1;
+    } else if (slab == 1) {
+        ox = clampi(q - R, 0, nx - 1); oy = face == 0 ? 0 : ny - 1; oz = p;
+    } else {
+        ox = face == 0 ? 0 : nx - 1; oy = q; oz = p;
     }
-    const int64_t idx = (static_cast<int64_t>(clampi(z, 0, nz - 1)) * ny + clampi(y, 0, ny - 1)) * nx +
-                        clampi(x, 0, nx - 1);
-    atomicAdd(out + idx, acc);
+    atomicAdd(out + (static_cast<int64_t>(oz) * ny + oy) * nx + ox, acc);
 }
 
 // One launch of the direct kernel over the job's region (forward) or over the padded
@@ -608,10 +669,8 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         if (e != cudaSuccess) return from_cuda(e);
         if constexpr (ADJ && R > 0) {
             // the shell outside the volumes, folded onto their faces after the main launch
-            const int64_t shell = 2LL * R *
-                                  ((job.ny + 2LL * R) * (job.nx + 2LL * R) + static_cast<int64_t>(job.nz) *
-                                   (job.nx + 2LL * R) + static_cast<int64_t>(job.nz) * job.ny);
-            k_adjoint_shell<K><<<dim3(static_cast<unsigned>((shell + 255) / 256), nv), 256, 0, ctx.stream>>>(
+            const int tiles = shell_tiles<K>(job.nx, job.ny, job.nz, nullptr, nullptr);
+            k_adjoint_shell<K><<<dim3(tiles, nv), SHELL_T * SHELL_T, 0, ctx.stream>>>(
                 static_cast<const float*>(a.src), static_cast<float*>(a.dst), job.nx, job.ny, job.nz,
                 a0.vs_src, a0.vs_dst, W);
             count_launches(1);

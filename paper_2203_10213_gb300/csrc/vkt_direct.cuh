@@ -598,14 +598,8 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int nvol = std::max(job.nvol, 1);
-    a.zchunk = job.zchunk > 0 ? std::min(job.zchunk, a.ez)
-                              : zchunk_for(static_cast<long>(gx) * gy * nvol, a.ez, sms);
-    const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
-    a.gzv = gz;
     a.vs_src = job.vs_src;
     a.vs_dst = job.vs_dst;
-    // one launch takes at most 65535 / gz volumes (the grid's z extent)
-    const int per_launch = std::max(1, 65535 / gz);
 
     alignas(64) CUtensorMap map;
     const int rawx = Geo::raw_w(job.sfmt);
@@ -614,7 +608,9 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         return encode_tensor_map(&map, job.sfmt, base, job.nx, job.ny, job.nz, nv, job.vs_src, rawx,
                                  Geo::FH, 1);
     };
-    a.use_tma = encode(job.src, std::min(nvol, per_launch)) ? 1 : 0;
+    // the tensor map spans the volumes of one launch, at most 65535 / gz (the grid's z extent);
+    // encoded for the whole batch first and re-encoded per launch once gz is known
+    a.use_tma = encode(job.src, std::min(nvol, 65535)) ? 1 : 0;
     if (!a.use_tma) memset(&map, 0, sizeof(map));
     // rows that no tensor map can describe are still fetched asynchronously, one bulk copy
     // per row, when every volume starts on a 16-byte boundary (forward only: the adjoint
@@ -653,6 +649,18 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return from_cuda(e);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    a.zchunk = job.zchunk > 0 ? std::min(job.zchunk, a.ez)
+                              : zchunk_direct(static_cast<long>(gx) * gy * nvol, a.ez, sms, per_sm, R);
+    const int gz = (a.ez + a.zchunk - 1) / a.zchunk;
+    a.gzv = gz;
+    const int per_launch = std::max(1, 65535 / gz);
+    if (a.use_tma && per_launch < nvol && !encode(job.src, per_launch)) return VKT_ERROR_CUDA;
     if (ctx.debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] direct%s k=%d grid=(%d,%d,%d) zchunk=%d smem=%zu tma=%d rows=%d withhold=%d\n",
                 ADJ ? "-adjoint" : (COMP ? "-compensated" : ""), K, gx, gy, gz, a.zchunk, smem,

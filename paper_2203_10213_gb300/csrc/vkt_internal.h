@@ -104,6 +104,39 @@ inline int zchunk_for(long tiles, int ez, int sms)
     return static_cast<int>((ez + chunks - 1) / chunks);
 }
 
+// z planes per CTA for `tiles` column tiles over ez planes, with `slots` CTAs resident at
+// once (SMs x CTAs per SM) and r halo planes on each side of a chunk: the chunk count whose
+// launch takes the least estimated time, waves x (planes per chunk + 2r), at least 8 planes
+// per chunk; ties go to fewer chunks (less halo).
+inline int zchunk_waves(long tiles, int ez, long slots, int r)
+{
+    slots = slots < 1 ? 1 : slots;
+    const long cap = ez / 8 < 1 ? 1 : ez / 8;
+    long best_cost = -1;
+    int best = ez;
+    for (long chunks = 1; chunks <= cap; ++chunks) {
+        const long z = (ez + chunks - 1) / chunks;
+        const long real = (ez + z - 1) / z;
+        const long waves = (tiles * real + slots - 1) / slots;
+        const long cost = waves * (z + 2 * r);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = static_cast<int>(z);
+        }
+    }
+    return best;
+}
+
+// The z chunk of a z-marching kernel (direct, adjoint): the wave-aware choice while chunks of
+// at least 8 planes still give every SM a CTA, else the short chunks of zchunk_for.
+inline int zchunk_direct(long tiles, int ez, int sms, int per_sm, int r)
+{
+    tiles = tiles < 1 ? 1 : tiles;
+    const long cap8 = ez / 8 < 1 ? 1 : ez / 8;
+    if (tiles * cap8 >= sms) return zchunk_waves(tiles, ez, static_cast<long>(sms) * per_sm, r);
+    return zchunk_for(tiles, ez, sms);
+}
+
 struct Ctx {
     cudaStream_t stream;
     int debug;

@@ -720,29 +720,5 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
     return true;
 }
 
-// z chunking that gives about 8 CTAs per SM in total over the bricks of one volume
-// z planes per CTA for `tiles` column tiles over nz planes, with `slots` CTAs resident at
-// once (SMs x CTAs per SM): the chunk count whose launch takes the least estimated time,
-// waves x (planes per chunk + 2r halo planes), at least 8 planes per chunk; ties go to
-// fewer chunks (less halo).
-inline int choose_zchunk(long tiles, int nz, long slots, int r)
-{
-    slots = slots < 1 ? 1 : slots;
-    const long cap = nz / 8 < 1 ? 1 : nz / 8;
-    long best_cost = -1;
-    int best = nz;
-    for (long chunks = 1; chunks <= cap; ++chunks) {
-        const long z = (nz + chunks - 1) / chunks;
-        const long real = (nz + z - 1) / z;
-        const long waves = (tiles * real + slots - 1) / slots;
-        const long cost = waves * (z + 2 * r);
-        if (best_cost < 0 || cost < best_cost) {
-            best_cost = cost;
-            best = static_cast<int>(z);
-        }
-    }
-    return best;
-}
-
 }  // namespace sep
 }  // namespace vkt

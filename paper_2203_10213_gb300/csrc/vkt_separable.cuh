@@ -173,7 +173,7 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast, sep::NT, smem);
     if (e != cudaSuccess) return from_cuda(e);
     J.zchunk = job.zchunk > 0 ? std::min(job.zchunk, ez)
-                             : sep::choose_zchunk(static_cast<long>(J.tiles_x) * J.tiles_y, ez,
+                             : zchunk_waves(static_cast<long>(J.tiles_x) * J.tiles_y, ez,
                                                   static_cast<long>(sms) * std::max(per_sm, 1), Geo::R);
     J.chunks = (ez + J.zchunk - 1) / J.zchunk;
     if (ctx.debug & VKT_DEBUG_LOG)

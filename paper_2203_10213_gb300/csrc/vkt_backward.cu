@@ -40,24 +40,33 @@ constexpr size_t wgrad_smem_bytes()
 {
     using Geo = Brick<K, TX, TY>;
     return 128 + static_cast<size_t>(STAGES) * Geo::raw_bytes(FMT_F32) +
-           2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float) +
            static_cast<size_t>(NT / 32) * K * K * sizeof(float);
 }
 
+// The FMAs read the raw float32 stage as delivered (no float tile): a window row is read as
+// NQ aligned float4s from the thread's column 4 tx on, and window element a of output x is
+// raw column 4 tx + x + a + XA - r.  Rows are clamped through the row each window row reads;
+// columns outside the volume (zero-filled by the tensor map) are overwritten with the face
+// column in the tiles at the x faces.  A stage is refilled only after the CTA barrier that
+// follows the FMAs reading it, so STAGES - 1 planes are in flight.
 template <int K>
 __global__ void __launch_bounds__(NT)
     k_wgrad(const __grid_constant__ CUtensorMap tmap, const WgArgs p)
 {
     using Geo = Brick<K, TX, TY>;
-    constexpr int R = Geo::R, FH = Geo::FH, FP = Geo::FP;
+    constexpr int R = Geo::R, FH = Geo::FH;
+    constexpr int XA = 4;                                  // float32 x halo of the raw tile
+    constexpr int RW = Geo::raw_w(FMT_F32);                // TX + 2 XA floats per raw row
+    constexpr int NW = RX + K - 1;                         // window row length
+    constexpr int NQ = (NW + XA - R + 3) / 4;              // float4 loads per window row
+    static_assert(RX * (BX - 1) + 4 * NQ <= RW, "window loads stay inside the raw row");
     __builtin_assume(threadIdx.x < NT);   // every launch has NT threads
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     constexpr int rawb = Geo::raw_bytes(FMT_F32);
     constexpr uint32_t txb = Geo::raw_tx(FMT_F32);
     unsigned char* raw = smem + 128;
-    float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
-    float* red = F + 2 * FH * FP;
+    float* red = reinterpret_cast<float*>(raw + STAGES * rawb);
 
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int tx = tid % BX, ty = tid / BX;
@@ -71,7 +80,6 @@ __global__ void __launch_bounds__(NT)
     const float* gyv = p.gy + vol * p.vs_gy;
     const int zc1 = min(zc0 + p.zchunk, p.nz);
     const int nplanes = max(zc1 - zc0, 0);
-    constexpr int xa = 4;     // float32 x halo that keeps the TMA box 16-byte aligned
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
@@ -81,15 +89,40 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();
     int issued = 0;
     // x plane paired with gy plane z is clamp(z + c - r)
-    if (p.use_tma && tid == 0) {
-        for (int s = 0; s < STAGES && s < nplanes; ++s, ++issued) {
-            mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(zc0 + s + c - R, 0, p.nz - 1), vol);
+    auto issue = [&](int q) {
+        const int s = q % STAGES;
+        mbar_arrive_expect_tx(&bars[s], txb);
+        tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - XA, y0 - R,
+                    clampi(zc0 + q + c - R, 0, p.nz - 1), vol);
+        ++issued;
+    };
+    if (p.use_tma && tid == 0)
+        for (int q = 0; q < STAGES - 1 && q < nplanes; ++q) issue(q);
+
+    // raw offset of each window row of this thread (rows clamped to the volume)
+    int rowoff[RY + K - 1];
+#pragma unroll
+    for (int j = 0; j < RY + K - 1; ++j)
+        rowoff[j] = (clampi(y0 - R + ty * RY + j, 0, p.ny - 1) - (y0 - R)) * RW + tx * RX;
+    // tensor-map stages at the x faces: raw columns [0, lfix) lie left of x = 0 and take
+    // column XA (x = 0); columns [rfix, RW) lie right of nx - 1 and take column rfix - 1;
+    // only the raw rows inside the volume, [ry0, ry1), are ever read
+    const int lfix = max(0, XA - x0);
+    const int rfix = min(RW, p.nx - x0 + XA);
+    const int ry0 = max(0, R - y0), ry1 = min(FH, p.ny - y0 + R);
+    const bool edge = p.use_tma && (lfix > 0 || rfix < RW);
+    auto fix_faces = [&](float* rf) {
+        const int nr = RW - rfix, per = lfix + nr;
+        for (int e = tid; e < (ry1 - ry0) * per; e += NT) {
+            const int r = ry0 + e / per, k = e % per;
+            float* row = rf + r * RW;
+            if (k < lfix)
+                row[k] = row[XA];
+            else
+                row[rfix + k - lfix] = row[rfix - 1];
         }
-    }
-    ConvPlan<Geo, NT> plan;
-    plan.init(FMT_F32, p.nx, p.ny, x0, y0, tid);
+        fence_proxy_async();   // a later tensor-map load refills these bytes
+    };
 
     float acc[K][K];
 #pragma unroll
@@ -117,33 +150,34 @@ __global__ void __launch_bounds__(NT)
     for (int it = 0; it < nplanes; ++it) {
         const int s = it % STAGES;
         const int z = zc0 + it;
-        const unsigned char* rs = raw + s * rawb;
-        float* Fb = F + (it & 1) * FH * FP;
+        unsigned char* rs = raw + s * rawb;
         bool ok = true;
         if (p.use_tma) {
             ok = mbar_wait(&bars[s], (it / STAGES) & 1);
+            if (ok && edge) fix_faces(reinterpret_cast<float*>(rs));
         } else {
-            fill_raw_plain<Geo, NT>(const_cast<unsigned char*>(rs), xv, FMT_F32,
-                                    p.nx, p.ny, p.nz, x0, y0, z + c - R, tid);
-            __syncthreads();
+            fill_raw_plain<Geo, NT>(rs, xv, FMT_F32, p.nx, p.ny, p.nz, x0, y0, z + c - R, tid);
         }
-        if (ok) plan.convert(rs, FMT_F32, Fb, tid);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
         }
-        if (p.use_tma && tid == 0 && it + STAGES < nplanes) {
-            mbar_arrive_expect_tx(&bars[s], txb);
-            tma_load_4d(raw + s * rawb, &tmap, &bars[s], x0 - xa, y0 - R,
-                        clampi(zc0 + it + STAGES + c - R, 0, p.nz - 1), vol);
-            ++issued;
-        }
+        // every thread is past the FMAs of plane it - 1: its stage takes plane it + STAGES - 1
+        if (p.use_tma && tid == 0 && it + STAGES - 1 < nplanes) issue(it + STAGES - 1);
         float gn[RY][RX];
         if (it + 1 < nplanes) load_g(z + 1, gn);
+        const float* rf = reinterpret_cast<const float*>(rs);
 #pragma unroll
         for (int j = 0; j < RY + K - 1; ++j) {
-            float win[RX + K - 1];
-            load_row<RX + K - 1, RX>(Fb + (ty * RY + j) * FP + tx * RX, win);
+            float q[4 * NQ];
+#pragma unroll
+            for (int n = 0; n < NQ; ++n) {
+                const float4 t = *reinterpret_cast<const float4*>(rf + rowoff[j] + 4 * n);
+                q[4 * n] = t.x;
+                q[4 * n + 1] = t.y;
+                q[4 * n + 2] = t.z;
+                q[4 * n + 3] = t.w;
+            }
 #pragma unroll
             for (int i = 0; i < RY; ++i) {
                 const int b = j - i;
@@ -151,7 +185,8 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                 for (int a = 0; a < K; ++a)
 #pragma unroll
-                    for (int x = 0; x < RX; ++x) acc[b][a] = fmaf(g[i][x], win[x + a], acc[b][a]);
+                    for (int x = 0; x < RX; ++x)
+                        acc[b][a] = fmaf(g[i][x], q[x + a + XA - R], acc[b][a]);
             }
         }
         if (it + 1 < nplanes) {

@@ -77,6 +77,7 @@ def test_policy_roundtrip(vkt, lib):
     assert lib.vktSetThreadExecutionPolicy(pol) == 0
 
 
+@without_device
 def test_volume_argument_validation(vkt, lib):
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(0x10000)

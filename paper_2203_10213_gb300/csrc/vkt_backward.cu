@@ -1,12 +1,13 @@
 // vkt_backward.cu -- gradients of the float32 clamped correlation y = C_w x:
-//   dL/dx : exact adjoint, evaluated by the direct kernel in adjoint mode (vkt_direct.cu);
+//   dL/dx : exact adjoint, evaluated by the direct kernel in adjoint mode (vkt_direct.cuh);
 //   dL/dw[c][b][a] = sum_i gy(i) x(clamp(i + (a-r, b-r, c-r))), evaluated here.
 //
 // Weight gradient: CTA (c, x tile, y tile, z chunk) owns one kernel plane offset c and a
-// 64 x 32 x zchunk brick of output positions i.  It streams the x planes z + c - r (TMA,
-// clamp-to-edge conversion into a float tile, recomputed from HBM instead of stored) and
-// the gy planes z, and accumulates the k^2 sums over (b, a) in registers: k^2 FMAs per
-// voxel per CTA, k^3 over the k CTAs that share a tile.  The CTA reduces its sums (warp
+// 64 x 32 x zchunk brick of output positions i.  It streams the x planes z + c - r (TMA into
+// a ring of raw float32 stages that the FMAs read directly, clamp-to-edge applied by row
+// index and, at the x faces, by patching the columns outside the volume in place) and the
+// gy planes z, and accumulates the k^2 sums over (b, a) in registers: k^2 FMAs per voxel
+// per CTA, k^3 over the k CTAs that share a tile.  The CTA reduces its sums (warp
 // shuffles, then shared memory) to one FP32 partial per tap; a second kernel adds the
 // partials of all CTAs in FP64 and writes float32 dL/dw.
 #include <algorithm>

@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(NT)
         if (LM != LM_ROWS && p.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
+    // set-up done: wait for the previous kernel on the stream (programmatic launch), let
+    // the next one start its set-up
+    grid_dependency_wait();
+    launch_dependents();
     int issued = 0;   // planes handed to the TMA unit so far (thread 0 only)
     const uint64_t vol_bytes = static_cast<uint64_t>(p.nx) * p.ny * p.nz * fmt_bytes(sfmt);
     if (tma && tid == 0) {
@@ -671,9 +675,9 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         a.src = static_cast<const unsigned char*>(a0.src) + v0 * a0.vs_src * es;
         a.dst = static_cast<unsigned char*>(a0.dst) + v0 * a0.vs_dst * (ADJ ? 4 : fmt_bytes(job.dfmt));
         if (v0 > 0 && a.use_tma && !encode(a.src, nv)) return VKT_ERROR_CUDA;
-        kern<<<dim3(gx, gy, gz * nv), NT, smem, ctx.stream>>>(map, a, W);
+        e = launch_pdl(kern, dim3(gx, gy, gz * nv), dim3(NT), smem, ctx.stream, map, a, W);
         count_launches(1);
-        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return from_cuda(e);
         if constexpr (ADJ && R > 0) {
             // the shell outside the volumes, folded onto their faces after the main launch

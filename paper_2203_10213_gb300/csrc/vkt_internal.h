@@ -1,6 +1,7 @@
 // vkt_internal.h -- host-side structures shared by the runtime and the kernel launchers.
 #pragma once
 
+#include <utility>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
@@ -135,6 +136,26 @@ inline int zchunk_direct(long tiles, int ez, int sms, int per_sm, int r)
     const long cap8 = ez / 8 < 1 ? 1 : ez / 8;
     if (tiles * cap8 >= sms) return zchunk_waves(tiles, ez, static_cast<long>(sms) * per_sm, r);
     return zchunk_for(tiles, ez, sms);
+}
+
+// Launches `kern` with programmatic stream serialization: the kernel may start while the
+// previous kernel on the stream finishes, and must call grid_dependency_wait() before it
+// touches global memory.
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
 struct Ctx {

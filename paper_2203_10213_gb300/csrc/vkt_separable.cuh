@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(sep::NT, sep_min_blocks<K, SF>())
         if (LM != sep::LM_ROWS && J.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
+    grid_dependency_wait();   // programmatic launch: the previous kernel's writes are visible
+    launch_dependents();
     uint32_t gplane = 0;   // this CTA's only brick: the static ring applies when NS == K
     constexpr int NS = ns_of<K, LM, ROI>();
     sep::brick<K, sep::W<K>, SF, DF, LM, ROI, NS, NS == K>(J, G, &tmap, blockIdx.x, blockIdx.y,
@@ -54,6 +56,8 @@ __global__ void __launch_bounds__(sep::NT)
         if (LM != sep::LM_ROWS && J.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
+    grid_dependency_wait();   // programmatic launch: the previous kernel's writes are visible
+    launch_dependents();
     uint32_t gplane = 0;
     sep::brick_comp<K, sep::W<K>, LM, ROI>(J, G, &tmap, blockIdx.x, blockIdx.y, blockIdx.z, smem,
                                            gplane, status);
@@ -181,11 +185,10 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
                 J.comp ? "-compensated" : "", K, J.tiles_x, J.tiles_y, J.chunks, J.zchunk, smem,
                 J.use_tma, J.rows);
     const dim3 grid(J.tiles_x, J.tiles_y, J.chunks);
-    if (J.comp)
-        comp<<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
-    else
-        fast<<<grid, sep::NT, smem, ctx.stream>>>(map, J, G, ctx.status);
+    e = J.comp ? launch_pdl(comp, grid, dim3(sep::NT), smem, ctx.stream, map, J, G, ctx.status)
+               : launch_pdl(fast, grid, dim3(sep::NT), smem, ctx.stream, map, J, G, ctx.status);
     count_launches(1);
+    if (e != cudaSuccess) return from_cuda(e);
     return from_cuda(cudaGetLastError());
 }
 

@@ -41,6 +41,22 @@ __device__ __forceinline__ void fence_mbar_init()
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization
+// (launch_pdl) may begin while the kernel before it on the stream is still running: it sets
+// up its shared memory and barriers, then waits in grid_dependency_wait() until that kernel
+// has completed and its writes are visible, before its first global-memory access.
+// launch_dependents() lets the next such kernel begin its own set-up once every CTA of this
+// grid is running.
+__device__ __forceinline__ void grid_dependency_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+__device__ __forceinline__ void launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // orders this thread's generic-proxy writes to shared memory before later async-proxy
 // (TMA) writes to the same bytes
 __device__ __forceinline__ void fence_proxy_async()

@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(NT)
         if (p.use_tma) prefetch_tensor_map(&tmap);
     }
     __syncthreads();
+    grid_dependency_wait();   // programmatic launch: the previous kernel's writes are visible
+    launch_dependents();
     int issued = 0;
     // x plane paired with gy plane z is clamp(z + c - r)
     auto issue = [&](int q) {
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(NT)
 __global__ void k_wgrad_reduce(const float* partials, int nspatial, int kkk, float* gw,
                                const unsigned* failed)
 {
+    grid_dependency_wait();   // programmatic launch: the partial sums are written
     const int d = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
     if (d >= kkk) return;
@@ -302,8 +305,10 @@ vktError launch_wg_partials(const float* x, const float* gy, int nx, int ny, int
     if (debug & VKT_DEBUG_LOG)
         fprintf(stderr, "[vkt] wgrad k=%d grid=(%d,%d,%d) zchunk=%d volumes=%d tma=%d\n", K,
                 g.tiles_x * K, g.tiles_y, g.chunks * nvol, g.zchunk, nvol, a.use_tma);
-    k_wgrad<K><<<dim3(g.tiles_x * K, g.tiles_y, g.chunks * nvol), NT, smem, stream>>>(map, a);
+    e = launch_pdl(k_wgrad<K>, dim3(g.tiles_x * K, g.tiles_y, g.chunks * nvol), dim3(NT), smem,
+                   stream, map, a);
     count_launches(1);
+    if (e != cudaSuccess) return from_cuda(e);
     return from_cuda(cudaGetLastError());
 }
 
@@ -311,8 +316,8 @@ void launch_reduce(const float* partials, size_t nspatial, int k, float* gw, con
                    cudaStream_t stream)
 {
     const int kkk = k * k * k;
-    k_wgrad_reduce<<<(kkk + 7) / 8, 256, 0, stream>>>(partials, static_cast<int>(nspatial), kkk, gw,
-                                                       failed);
+    launch_pdl(k_wgrad_reduce, dim3((kkk + 7) / 8), dim3(256), 0, stream, partials,
+               static_cast<int>(nspatial), kkk, gw, failed);
     count_launches(1);
 }
 

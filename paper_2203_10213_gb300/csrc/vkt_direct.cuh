@@ -475,6 +475,9 @@ __global__ void __launch_bounds__(SHELL_T * SHELL_T)
         }
         fw[face][axis][q] = sum;
     }
+    // programmatic launch: the main adjoint launch's stores are complete and visible
+    grid_dependency_wait();
+    launch_dependents();
     // this CTA's slab (0: z, 1: y, 2: x), face and tile
     int na = 0, nb = 0;
     shell_tiles<K>(nx, ny, nz, &na, &nb);
@@ -682,11 +685,11 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         if constexpr (ADJ && R > 0) {
             // the shell outside the volumes, folded onto their faces after the main launch
             const int tiles = shell_tiles<K>(job.nx, job.ny, job.nz, nullptr, nullptr);
-            k_adjoint_shell<K><<<dim3(tiles, nv), SHELL_T * SHELL_T, 0, ctx.stream>>>(
-                static_cast<const float*>(a.src), static_cast<float*>(a.dst), job.nx, job.ny, job.nz,
-                a0.vs_src, a0.vs_dst, W);
+            e = launch_pdl(k_adjoint_shell<K>, dim3(tiles, nv), dim3(SHELL_T * SHELL_T), 0, ctx.stream,
+                           static_cast<const float*>(a.src), static_cast<float*>(a.dst), job.nx,
+                           job.ny, job.nz, a0.vs_src, a0.vs_dst, W);
             count_launches(1);
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGetLastError();
             if (e != cudaSuccess) return from_cuda(e);
         }
     }

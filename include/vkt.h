@@ -140,7 +140,8 @@ VKT_API const char* vktGetErrorString(vktError error);
  * Waits for the policy stream and reports device-side failures recorded since the last
  * call: VKT_ERROR_DEVICE_TIMEOUT if a bounded wait inside a kernel gave up (the kernel
  * then skipped its work and its output is undefined), VKT_ERROR_CUDA on an asynchronous
- * CUDA error.  Clears the recorded device status.
+ * CUDA error or when a kernel found its launch inconsistent with the tile shape it was
+ * built for (it then skipped its work).  Clears the recorded device status.
  */
 VKT_API vktError vktSynchronize(void);
 

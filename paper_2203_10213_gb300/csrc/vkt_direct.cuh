@@ -73,10 +73,12 @@ struct DirectArgs {
     unsigned* status;
 };
 
-template <int K, bool COMP = false>
+// SHAPE 1: one output row per thread (64 x 16 tiles) for the plain k <= 3 kernels of
+// volumes too small to give every SM a CTA (64^3: 4 tiles per plane instead of 1)
+template <int K, bool COMP = false, int SHAPE = 0>
 struct DirectCfg {
     static constexpr int RX = (K == 9 || (COMP && K >= 7)) ? 2 : 4;
-    static constexpr int RY = COMP ? 1 : ((K <= 3) ? 4 : 2);
+    static constexpr int RY = (COMP || SHAPE == 1) ? 1 : ((K <= 3) ? 4 : 2);
     static constexpr bool ROT = K >= 5;
     // PAIR: the x taps run as packed two-lane FMAs over neighbouring outputs (x, x+1),
     // which halves the FMA instructions of a kernel whose time is instruction issue
@@ -85,10 +87,10 @@ struct DirectCfg {
     using Geo = Brick<K, TX, TY>;
 };
 
-template <int K, bool COMP = false>
+template <int K, bool COMP = false, int SHAPE = 0>
 __host__ __device__ constexpr size_t direct_smem_bytes(int sfmt, bool rows)
 {
-    using Geo = typename DirectCfg<K, COMP>::Geo;
+    using Geo = typename DirectCfg<K, COMP, SHAPE>::Geo;
     return 128 + static_cast<size_t>(STAGES) * Geo::stage_bytes(sfmt, rows) +
            2 * static_cast<size_t>(Geo::FH) * Geo::FP * sizeof(float);
 }
@@ -102,12 +104,12 @@ constexpr int LM_ANY = 0, LM_TMA = 1, LM_ROWS = 2;
 // volume (known at compile time to start at column 0).  COMP: compensated accumulation
 // into an integer destination (forward only).
 template <int K, bool ADJ, int SF = -1, int DF = -1, int LM = LM_ANY, bool ROI = false,
-          bool COMP = false>
+          bool COMP = false, int SHAPE = 0>
 __global__ void __launch_bounds__(NT)
     k_direct(const __grid_constant__ CUtensorMap tmap, const DirectArgs p, const DenseW<K> W)
 {
     static_assert(!(COMP && ADJ), "the adjoint writes float32");
-    using Cfg = DirectCfg<K, COMP>;
+    using Cfg = DirectCfg<K, COMP, SHAPE>;
     using Geo = typename Cfg::Geo;
     constexpr int R = Geo::R, RX = Cfg::RX, RY = Cfg::RY;
     constexpr int FH = Geo::FH, FP = Geo::FP;
@@ -122,6 +124,13 @@ __global__ void __launch_bounds__(NT)
     const uint32_t txb = Geo::raw_tx(sfmt);
     unsigned char* raw = smem + 128;
     float* F = reinterpret_cast<float*>(raw + STAGES * rawb);
+    // a launch whose shared memory was sized for another tile shape records the mismatch
+    // and does nothing (instead of running past the end of its shared memory)
+    if (dynamic_smem_bytes() < direct_smem_bytes<K, COMP, SHAPE>(sfmt, rows)) {
+        grid_dependency_wait();
+        if (threadIdx.x == 0) atomicOr(p.status, STATUS_CONFIG);
+        return;
+    }
 
     const int tid = threadIdx.x;
     const int tx = tid % BX, ty = tid / BX;
@@ -544,13 +553,27 @@ __global__ void __launch_bounds__(SHELL_T * SHELL_T)
     atomicAdd(out + (static_cast<int64_t>(oz) * ny + oy) * nx + ox, acc);
 }
 
+// True if the job's default k <= 3 tiles (64 x 64), in chunks of at least 8 planes, give
+// fewer CTAs than the GPU has SMs: the one-row-per-thread shape then runs 4x as many CTAs.
+inline bool direct_small(const Job& job)
+{
+    int rx0, ry0, rz0, rx1, ry1, rz1;
+    job_region(job, rx0, ry0, rz0, rx1, ry1, rz1);
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long tiles = static_cast<long>((rx1 - rx0 + 63) / 64) * ((ry1 - ry0 + 63) / 64) *
+                       std::max(job.nvol, 1);
+    const long cap8 = std::max((rz1 - rz0) / 8, 1);
+    return tiles * cap8 < sms;
+}
+
 // One launch of the direct kernel over the job's region (forward) or over the padded
 // domain (adjoint); COMP: compensated accumulation into an integer destination.
-template <int K, bool ADJ, bool COMP = false>
+template <int K, bool ADJ, bool COMP = false, int SHAPE = 0>
 vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
 {
     static_assert(!(COMP && ADJ), "the adjoint writes float32");
-    using Cfg = DirectCfg<K, COMP>;
+    using Cfg = DirectCfg<K, COMP, SHAPE>;
     using Geo = typename Cfg::Geo;
     constexpr int R = Geo::R;
     DirectArgs a;
@@ -627,30 +650,30 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
                  ? 1
                  : 0;
 
-    const size_t smem = direct_smem_bytes<K, COMP>(job.sfmt, a.rows != 0);
+    const size_t smem = direct_smem_bytes<K, COMP, SHAPE>(job.sfmt, a.rows != 0);
     // the common float32 destinations get kernels with their formats compiled in
     // tensor-map jobs get kernels without the other ways of loading, and so do row-copy
     // jobs of the compiled-in formats; plain-load jobs take the run-time variant
-    auto kern = a.use_tma ? k_direct<K, ADJ, -1, -1, LM_TMA, false, COMP>
-                          : k_direct<K, ADJ, -1, -1, LM_ANY, false, COMP>;
+    auto kern = a.use_tma ? k_direct<K, ADJ, -1, -1, LM_TMA, false, COMP, SHAPE>
+                          : k_direct<K, ADJ, -1, -1, LM_ANY, false, COMP, SHAPE>;
     if constexpr (!ADJ) {
-        if (job.roi) kern = k_direct<K, ADJ, -1, -1, LM_ANY, true, COMP>;   // reads the region fields
+        if (job.roi) kern = k_direct<K, ADJ, -1, -1, LM_ANY, true, COMP, SHAPE>;   // reads the region fields
     }
     if constexpr (!ADJ && !COMP && K >= 3 && K <= 5) {
         // region tensor-map jobs of the common float32 destinations: formats compiled in
         if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_U8)
-            kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, true>;
+            kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, true, false, SHAPE>;
         if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_F32)
-            kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, true>;
+            kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, true, false, SHAPE>;
     }
     if constexpr (!ADJ && !COMP && K >= 3 && K <= 5) {
         if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
-            if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA>;
-            else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS>;
+            if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, false, false, SHAPE>;
+            else if (a.rows) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_ROWS, false, false, SHAPE>;
         }
         if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_F32) {
-            if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA>;
-            else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS>;
+            if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, false, false, SHAPE>;
+            else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS, false, false, SHAPE>;
         }
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

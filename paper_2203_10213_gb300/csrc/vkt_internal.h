@@ -158,6 +158,10 @@ cudaError_t launch_pdl(void (*kern)(Params...), dim3 grid, dim3 block, size_t sm
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// bits of the device status word (Ctx::status), reported by vktSynchronize
+constexpr unsigned STATUS_TIMEOUT = 1u;   // a bounded device wait gave up
+constexpr unsigned STATUS_CONFIG = 2u;    // a kernel found its launch inconsistent with its build
+
 struct Ctx {
     cudaStream_t stream;
     int debug;

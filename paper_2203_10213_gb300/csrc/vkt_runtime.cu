@@ -335,7 +335,7 @@ vktError vktSynchronize(void)
         e = cudaMemsetAsync(ctx.status, 0, sizeof(st), ctx.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx.stream);
         if (e != cudaSuccess) return from_cuda(e);
-        return VKT_ERROR_DEVICE_TIMEOUT;
+        return (st & STATUS_TIMEOUT) ? VKT_ERROR_DEVICE_TIMEOUT : VKT_ERROR_CUDA;
     }
     return VKT_NO_ERROR;
 }

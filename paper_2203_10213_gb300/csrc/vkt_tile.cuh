@@ -11,7 +11,6 @@ namespace vkt {
 
 enum : int { FMT_U8 = 0, FMT_U16 = 1, FMT_F32 = 2 };
 
-constexpr unsigned STATUS_TIMEOUT = 1u;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s for any single device wait
 
 __host__ __device__ constexpr int fmt_bytes(int f) { return f == FMT_U8 ? 1 : (f == FMT_U16 ? 2 : 4); }
@@ -39,6 +38,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 __device__ __forceinline__ void fence_mbar_init()
 {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// bytes of dynamic shared memory this CTA was launched with
+__device__ __forceinline__ uint32_t dynamic_smem_bytes()
+{
+    uint32_t v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
 }
 
 // Programmatic dependent launch.  A kernel launched with programmatic stream serialization

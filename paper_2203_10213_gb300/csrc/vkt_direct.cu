@@ -11,7 +11,7 @@ vktError launch_direct(const Job& job, const float* w, int k, const Ctx& ctx)
     switch (k) {
     case 1: return dir::launch_k<1, false>(job, w, ctx);
     case 3:
-        return dir::direct_small(job) ? dir::launch_k<3, false, false, 1>(job, w, ctx)
+        return dir::direct_small(job, ctx.sms) ? dir::launch_k<3, false, false, 1>(job, w, ctx)
                                       : dir::launch_k<3, false>(job, w, ctx);
     case 5: return dir::launch_k<5, false>(job, w, ctx);
     case 7: return dir::launch_k<7, false>(job, w, ctx);

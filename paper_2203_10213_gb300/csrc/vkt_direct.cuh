@@ -555,12 +555,10 @@ __global__ void __launch_bounds__(SHELL_T * SHELL_T)
 
 // True if the job's default k <= 3 tiles (64 x 64), in chunks of at least 8 planes, give
 // fewer CTAs than the GPU has SMs: the one-row-per-thread shape then runs 4x as many CTAs.
-inline bool direct_small(const Job& job)
+inline bool direct_small(const Job& job, int sms)
 {
     int rx0, ry0, rz0, rx1, ry1, rz1;
     job_region(job, rx0, ry0, rz0, rx1, ry1, rz1);
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long tiles = static_cast<long>((rx1 - rx0 + 63) / 64) * ((ry1 - ry0 + 63) / 64) *
                        std::max(job.nvol, 1);
     const long cap8 = std::max((rz1 - rz0) / 8, 1);
@@ -621,12 +619,7 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
 
     const int gx = (a.ex + Cfg::TX - 1) / Cfg::TX;
     const int gy = (a.ey + Cfg::TY - 1) / Cfg::TY;
-    int sms = 152;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = ctx.sms;
     const int nvol = std::max(job.nvol, 1);
     a.vs_src = job.vs_src;
     a.vs_dst = job.vs_dst;
@@ -676,15 +669,10 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
             else if (a.rows) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_ROWS, false, false, SHAPE>;
         }
     }
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return from_cuda(e);
     int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
+    const vktError ve = prepare_kernel(ctx, reinterpret_cast<const void*>(kern), NT, smem, &per_sm);
+    if (ve != VKT_NO_ERROR) return ve;
+    cudaError_t e = cudaSuccess;
     a.zchunk = job.zchunk > 0 ? std::min(job.zchunk, a.ez)
                               : zchunk_direct(static_cast<long>(gx) * gy * nvol, a.ez, sms, per_sm, R);
     const int gz = (a.ez + a.zchunk - 1) / a.zchunk;

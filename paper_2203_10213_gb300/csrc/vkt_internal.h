@@ -166,7 +166,14 @@ struct Ctx {
     cudaStream_t stream;
     int debug;
     unsigned* status;   // device status word of the current device
+    int device;         // the current device and its SM count
+    int sms;
 };
+
+// Sets `kern`'s dynamic shared memory limit to `smem` and returns its resident CTAs per SM
+// at `threads` threads (at least 1), once per (device, kernel, smem); later calls read the
+// remembered answer instead of asking the driver again.
+vktError prepare_kernel(const Ctx& ctx, const void* kern, int threads, size_t smem, int* per_sm);
 
 // Kernel launchers (each returns VKT_NO_ERROR or a launch error).  launch_direct takes
 // the compensated kernels when job.comp is set (launch_direct_comp).

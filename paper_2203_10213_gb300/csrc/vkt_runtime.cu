@@ -9,7 +9,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -26,6 +28,12 @@ std::atomic<uint64_t> g_launches{0};
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mutex;
 unsigned* g_status[MAX_DEVICES] = {};
+int g_sms[MAX_DEVICES] = {};
+// for prepare_kernel: (device, kernel, dynamic shared memory) -> resident CTAs per SM, and
+// (device, kernel) -> the largest dynamic shared memory limit set so far (the limit is never
+// lowered: a smaller setting would refuse a later launch that needs the larger one)
+std::map<std::tuple<int, const void*, size_t>, int> g_prepared;
+std::map<std::pair<int, const void*>, size_t> g_smem_limit;
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -145,10 +153,47 @@ vktError get_context(Ctx* ctx)
             }
             g_status[dev] = p;
         }
+        if (g_sms[dev] <= 0) {
+            int n = 0;
+            e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return from_cuda(e);
+            g_sms[dev] = n > 0 ? n : 1;
+        }
         ctx->status = g_status[dev];
+        ctx->sms = g_sms[dev];
     }
+    ctx->device = dev;
     ctx->stream = static_cast<cudaStream_t>(t_policy.stream);
     ctx->debug = t_policy.debug;
+    return VKT_NO_ERROR;
+}
+
+vktError prepare_kernel(const Ctx& ctx, const void* kern, int threads, size_t smem, int* per_sm)
+{
+    const auto key = std::make_tuple(ctx.device, kern, smem);
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        auto it = g_prepared.find(key);
+        if (it != g_prepared.end()) {
+            *per_sm = it->second;
+            return VKT_NO_ERROR;
+        }
+    }
+    std::lock_guard<std::mutex> lock(g_mutex);
+    size_t& limit = g_smem_limit[std::make_pair(ctx.device, kern)];
+    if (smem > limit) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   static_cast<int>(smem));
+        if (e != cudaSuccess) return from_cuda(e);
+        limit = smem;
+    }
+    int n = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    g_prepared[key] = n;
+    *per_sm = n;
     return VKT_NO_ERROR;
 }
 

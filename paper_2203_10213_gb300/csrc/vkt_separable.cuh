@@ -118,12 +118,7 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         G.gy[i] = gy[i];
         G.gz[i] = gz[i];
     }
-    int sms = 152;
-    {
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = ctx.sms;
     J.tiles_x = (ex + sep::TX - 1) / sep::TX;
     J.tiles_y = (ey + ty - 1) / ty;
 
@@ -164,18 +159,13 @@ vktError launch_k(const Job& job, const float* gx, const float* gy, const float*
         smem = std::max(smem, sep::smem_bytes_fx<K, K>(job.sfmt));
     if (!J.comp && J.use_tma && !job.roi && K >= 3 && K <= 7)
         smem = std::max(smem, sep::smem_bytes<K, K>(job.sfmt, false));
-    cudaError_t e = J.comp ? cudaFuncSetAttribute(comp,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  static_cast<int>(smem))
-                           : cudaFuncSetAttribute(fast,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  static_cast<int>(smem));
-    if (e != cudaSuccess) return from_cuda(e);
     // z chunks sized for whole waves of the CTAs the chosen kernel keeps resident
-    int per_sm = 0;
-    e = J.comp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, comp, sep::NT, smem)
-               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fast, sep::NT, smem);
-    if (e != cudaSuccess) return from_cuda(e);
+    int per_sm = 1;
+    vktError ve = prepare_kernel(ctx, J.comp ? reinterpret_cast<const void*>(comp)
+                                             : reinterpret_cast<const void*>(fast),
+                                 sep::NT, smem, &per_sm);
+    if (ve != VKT_NO_ERROR) return ve;
+    cudaError_t e = cudaSuccess;
     J.zchunk = job.zchunk > 0 ? std::min(job.zchunk, ez)
                              : zchunk_waves(static_cast<long>(J.tiles_x) * J.tiles_y, ez,
                                                   static_cast<long>(sms) * std::max(per_sm, 1), Geo::R);

@@ -377,14 +377,21 @@ def batching_form(args, vkt, torch, dev, stream):
             for i in range(len(items)):
                 vkt.check(lib.vktApplyFilterSV(vd[i].handle, vs[i].handle, fs[i].handle))
 
-        # the fixed rule (64-plane bricks, full occupancy), then the autotuned plan (its first
-        # call, untimed, measures the candidates)
+        # the fixed rule (64-plane bricks, full occupancy) and the autotuned plan (its first
+        # call, untimed, measures the candidates), timed in alternation and compared by
+        # their medians so that the drift of the GPU between two timings does not favour one
         enabled = ctypes.c_int32()
         vkt.check(lib.vktAutotuneGetEnabled(ctypes.byref(enabled)))
-        vkt.check(lib.vktAutotuneSetEnabled(0))
-        ms_rule = timed(batched)
         vkt.check(lib.vktAutotuneSetEnabled(1))
-        ms_batch = timed(batched)
+        batched()
+        torch.cuda.synchronize()
+        rule_ms, tuned_ms = [], []
+        for _ in range(5):
+            vkt.check(lib.vktAutotuneSetEnabled(0))
+            rule_ms.append(timed(batched))
+            vkt.check(lib.vktAutotuneSetEnabled(1))
+            tuned_ms.append(timed(batched))
+        ms_rule, ms_batch = statistics.median(rule_ms), statistics.median(tuned_ms)
         vkt.check(lib.vktAutotuneSetEnabled(enabled.value))
         ms_sep = timed(separate)
         # sum of individually timed launches

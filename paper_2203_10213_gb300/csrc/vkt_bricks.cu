@@ -16,6 +16,7 @@
 #include <memory>
 
 #include "vkt_internal.h"
+#include "vkt_tile.cuh"
 
 namespace vkt {
 namespace {
@@ -402,7 +403,184 @@ __global__ void __launch_bounds__(NT, BLK ? 6 : 5)
     }
 }
 
+// Plane-image variant, for ghost cells on a source a tensor map describes.  Brick plane k
+// (source plane clamp(oz - ghost + k)) is one contiguous run of dx * dy voxels in the brick,
+// and the source voxels it needs lie in one box: columns [ox - XA, ox + bx + XA) (XA = 16
+// bytes of voxels, so the box starts on a 16-byte boundary and holds ghost <= XA columns on
+// either side), rows [oy - ghost, oy + by + ghost).  A CTA takes a run of one brick's planes:
+// TMA brings each plane's box into a ring of stages (rows and columns outside the volume
+// arrive zero-filled, the z coordinate is clamped), and the threads write the brick plane as
+// words, lanes on consecutive words (one 128-byte store per warp): word c of brick row j is
+// staged row clamp(oy - ghost + j) - (oy - ghost), bytes (XA - ghost) * ES + 4c onward, one
+// funnel shift of two staged words (the shift is the same for every word of the launch).
+// Bricks whose ghost columns reach past an x face of the volume assemble each word voxel by
+// voxel from clamped columns instead.  Needs brick rows of whole words (dx * ES a multiple
+// of 4), 4-byte aligned bricks, and bx * ES a multiple of 16 (box starts on 16-byte
+// boundaries).  Every wait is bounded; on a timeout the CTA records it and drains its loads.
+constexpr int PL_STAGES = 4;
+
+struct PlaneArgs {
+    int ppc;             // brick planes per CTA
+    int boxw, boxh;      // box extent (voxels, rows)
+    int stage;           // bytes per stage (box bytes rounded up, with 16 bytes of slack)
+    uint32_t txb;        // bytes one box delivers
+    unsigned* status;
+};
+
+template <int ES>
+__global__ void __launch_bounds__(NT)
+    k_bricks_planes(const __grid_constant__ CUtensorMap tmap, const BrickPtrs P, const BrickGrid G,
+                    const PlaneArgs A)
+{
+    constexpr int XA = 16 / ES;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* ring = smem + 128;
+    const BrickDesc b = brick_at(P, G);
+    const int g = G.ghost;
+    const int k0 = blockIdx.x * A.ppc;
+    if (k0 >= b.dz) return;
+    const int np = min(b.dz, k0 + A.ppc) - k0;
+    const int tid = threadIdx.x;
+    const int rb = A.boxw * ES;                  // staged row bytes
+    const int wpr = (b.dx * ES) >> 2;            // words per brick row
+    const int nwords = wpr * b.dy;               // words per brick plane
+    const int bx0 = b.ox - XA, by0 = b.oy - g;   // box origin
+    const bool xin = b.ox - g >= 0 && b.ox + b.dx - g <= G.nx;
+    const bool yin = by0 >= 0 && by0 + b.dy <= G.ny;
+    if (tid == 0) {
+        for (int q = 0; q < PL_STAGES; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+        prefetch_tensor_map(&tmap);
+    }
+    __syncthreads();
+    int issued = 0;   // planes handed to the TMA unit (thread 0 only)
+    auto issue = [&](int q) {
+        const int s = q % PL_STAGES;
+        mbar_arrive_expect_tx(&bars[s], A.txb);
+        tma_load_3d(ring + s * A.stage, &tmap, &bars[s], bx0, by0,
+                    clampi(b.oz - g + k0 + q, 0, G.nz - 1));
+        ++issued;
+    };
+    if (tid == 0)
+        for (int q = 0; q < PL_STAGES && q < np; ++q) issue(q);
+    // the thread's words advance by NT words: DR rows and DC words
+    const int DR = NT / wpr, DC = NT - DR * wpr;
+    const int r0 = tid / wpr, c0 = tid - r0 * wpr;
+    const int off0 = (XA - g) * ES;               // staged byte of brick column 0
+    const uint32_t sh = 8u * static_cast<uint32_t>(off0 & 3);
+    uint32_t* dst = static_cast<uint32_t*>(b.dst);
+    bool failed = false;
+    for (int q = 0; q < np; ++q) {
+        const int s = q % PL_STAGES;
+        const bool ok = mbar_wait(&bars[s], (q / PL_STAGES) & 1);
+        if (ok) {
+            const unsigned char* st = ring + s * A.stage;
+            const uint32_t* sw = reinterpret_cast<const uint32_t*>(st);
+            uint32_t* dp = dst + static_cast<int64_t>(k0 + q) * nwords;
+            int r = r0, c = c0;
+            for (int w = tid; w < nwords; w += NT) {
+                const int sr = yin ? r : clampi(by0 + r, 0, G.ny - 1) - by0;
+                uint32_t v;
+                if (xin) {
+                    const int bo = sr * rb + off0 + 4 * c;
+                    v = __funnelshift_r(sw[bo >> 2], sw[(bo >> 2) + 1], sh);
+                } else {
+                    v = 0;
+#pragma unroll
+                    for (int e = 0; e < 4 / ES; ++e) {
+                        const int x = clampi(b.ox - g + (4 / ES) * c + e, 0, G.nx - 1);
+                        const unsigned char* sp = st + sr * rb + (x - bx0) * ES;
+                        const uint32_t t = ES == 1 ? *sp
+                                         : ES == 2 ? *reinterpret_cast<const uint16_t*>(sp)
+                                                   : *reinterpret_cast<const uint32_t*>(sp);
+                        v |= t << (8 * ES * e);
+                    }
+                }
+                __stcs(dp + w, v);
+                c += DC;
+                r += DR;
+                if (c >= wpr) {
+                    c -= wpr;
+                    ++r;
+                }
+            }
+        }
+        // every thread is done with stage s: it takes plane q + PL_STAGES
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0 && q + PL_STAGES < np) issue(q + PL_STAGES);
+    }
+    if (failed && tid == 0) {
+        atomicOr(A.status, STATUS_TIMEOUT);
+        for (int q = issued - 1; q >= 0 && q >= issued - PL_STAGES; --q)
+            mbar_wait(&bars[q % PL_STAGES], (q / PL_STAGES) & 1);
+    }
+}
+
 int bricks_along(int n, int b) { return (n + b - 1) / b; }
+
+// The plane-image kernel over every brick of a call (the caller checked its conditions and
+// encoded the tensor map with a box of (bx + 2 XA) x (by + 2 ghost) x 1 voxels).
+vktError launch_planes(const vktStructuredVolume* bricks, int numBricks, const BrickGrid& G0,
+                       int es, const CUtensorMap& map, int max_dz, const Ctx& ctx, int sms,
+                       int* launches)
+{
+    const int xa = 16 / es;
+    PlaneArgs A;
+    A.boxw = G0.bx + 2 * xa;
+    A.boxh = G0.by + 2 * G0.ghost;
+    A.txb = static_cast<uint32_t>(A.boxw) * es * A.boxh;
+    A.stage = static_cast<int>((A.txb + 16 + 127) & ~127u);
+    A.status = ctx.status;
+    const size_t smem = 128 + static_cast<size_t>(PL_STAGES) * A.stage;
+    const void* kern = es == 1 ? reinterpret_cast<const void*>(k_bricks_planes<1>)
+                     : es == 2 ? reinterpret_cast<const void*>(k_bricks_planes<2>)
+                               : reinterpret_cast<const void*>(k_bricks_planes<4>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return from_cuda(e);
+    // planes per CTA for whole waves of the resident CTAs: the least waves x (planes per CTA
+    // + 2, a CTA's set-up counted as planes)
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess)
+        per_sm = 1;
+    const int64_t slots = static_cast<int64_t>(sms) * std::max(per_sm, 1);
+    int64_t best = -1;
+    A.ppc = max_dz;
+    for (int c = 1; c <= max_dz; ++c) {
+        const int ppc = (max_dz + c - 1) / c;
+        const int64_t ctas = static_cast<int64_t>((max_dz + ppc - 1) / ppc) * numBricks;
+        const int64_t cost = ((ctas + slots - 1) / slots) * (ppc + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            A.ppc = ppc;
+        }
+    }
+    const int gx = (max_dz + A.ppc - 1) / A.ppc;
+    BrickGrid G = G0;
+    std::unique_ptr<BrickPtrs> P(new BrickPtrs);
+    for (int first = 0; e == cudaSuccess && first < numBricks; first += MAXB) {
+        const int nb = std::min(MAXB, numBricks - first);
+        for (int i = 0; i < nb; ++i) P->p[i] = bricks[first + i]->data;
+        G.first = first;
+        const dim3 grid(gx, nb);
+        if (es == 1)
+            k_bricks_planes<1><<<grid, NT, smem, ctx.stream>>>(map, *P, G, A);
+        else if (es == 2)
+            k_bricks_planes<2><<<grid, NT, smem, ctx.stream>>>(map, *P, G, A);
+        else
+            k_bricks_planes<4><<<grid, NT, smem, ctx.stream>>>(map, *P, G, A);
+        e = cudaGetLastError();
+        ++*launches;
+    }
+    if (ctx.debug & VKT_DEBUG_LOG)
+        fprintf(stderr, "[vkt] brick-decompose %d bricks (%dx%dx%d, ghost %d) grid=(%d,%d) planes=%d planes launches=%d\n",
+                numBricks, G0.bx, G0.by, G0.bz, G0.ghost, gx, std::min(numBricks, MAXB), A.ppc, *launches);
+    return from_cuda(e);
+}
 
 }  // namespace
 }  // namespace vkt
@@ -519,7 +697,6 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
         }
         rb = std::min(rb, rows_per_cta);
     }
-    const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
     BrickGrid G;
     G.nx = nx;
     G.ny = ny;
@@ -530,6 +707,32 @@ vktError vktBrickDecomposeSV(vktStructuredVolume* bricks, int32_t numBricks,
     G.cx = cx;
     G.cy = cy;
     G.ghost = ghost;
+    // ghost cells on a source a tensor map describes: the plane-image kernel, when the brick
+    // width starts every box on a 16-byte boundary, the ghosts fit the box's 16-byte x halo,
+    // the bricks are 4-byte aligned with rows of whole words, and the ring fits shared memory
+    {
+        const int pxa = 16 / es;
+        bool planes = ghost >= 1 && ghost <= pxa && (static_cast<int64_t>(brickX) * es) % 16 == 0 &&
+                      brickX + 2 * pxa <= 256 && brickY + 2 * ghost <= 256 &&
+                      static_cast<int64_t>(brickX + 2 * pxa) * es * (brickY + 2 * ghost) <= 40 * 1024;
+        int max_dz = 0;
+        for (int i = 0; planes && i < numBricks; ++i) {
+            planes = (reinterpret_cast<uintptr_t>(bricks[i]->data) & 3) == 0 &&
+                     (static_cast<int64_t>(bricks[i]->dims[0]) * es) % 4 == 0;
+            max_dz = std::max(max_dz, bricks[i]->dims[2]);
+        }
+        alignas(64) CUtensorMap pmap;
+        if (planes)
+            planes = encode_tensor_map_3d(&pmap, volume->format, volume->data, nx, ny, nz,
+                                          brickX + 2 * pxa, brickY + 2 * ghost, 1);
+        if (planes) {
+            int launches = 0;
+            const vktError pe = launch_planes(bricks, numBricks, G, es, pmap, max_dz, ctx, sms, &launches);
+            count_launches(launches);
+            return pe;
+        }
+    }
+    const int gx = (max_rows + rows_per_cta - 1) / rows_per_cta;
     std::unique_ptr<BrickPtrs> P(new BrickPtrs);
     cudaError_t e = cudaSuccess;
     int launches = 0;

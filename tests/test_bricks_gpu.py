@@ -49,6 +49,39 @@ def test_bricks_match_oracle(fmt, shape, brick, ghost):
         assert np.array_equal(g.view(np.uint8), np.ascontiguousarray(r).view(np.uint8)), f"brick {i}"
 
 
+@pytest.mark.parametrize("fmt,shape,brick,ghost", [
+    (synth.U8, (37, 45, 64), (16, 16, 16), 2),    # faces on every axis, partial bricks in y, z
+    (synth.U8, (20, 30, 80), (32, 10, 6), 4),     # the last brick along x is partial (16 wide)
+    (synth.U8, (9, 40, 48), (16, 8, 4), 16),      # the widest ghost the 16-byte halo holds
+    (synth.U16, (25, 19, 40), (8, 8, 8), 2),
+    (synth.U16, (10, 12, 16), (8, 5, 4), 1),      # 20-byte rows: shifts of 2 bytes
+    (synth.U16, (6, 7, 24), (8, 4, 3), 8),
+    (synth.F32, (21, 22, 28), (12, 8, 8), 3),     # partial last brick along x
+    (synth.F32, (13, 9, 32), (4, 4, 5), 4),
+    (synth.F32, (8, 6, 16), (4, 3, 2), 1),
+])
+def test_plane_image_kernel(fmt, shape, brick, ghost, capfd):
+    """Ghost cells on a source a tensor map describes, brick widths of whole 16-byte blocks
+    and brick rows of whole words take the plane-image kernel (one box per brick plane, one
+    funnel shift per word, voxel-by-voxel words at the x faces): bit-exact against the
+    oracle for every format, ghost widths up to the 16-byte halo, partial bricks and
+    clamping on every face."""
+    src = volume(fmt, shape, SEED + 31 + sum(shape) + ghost)
+    capfd.readouterr()
+    with vkt.policy(debug=vkt.DEBUG_LOG):
+        got = vkt.brick_decompose(torch.from_numpy(src).cuda(), brick, ghost)
+        torch.cuda.synchronize()
+    err = capfd.readouterr().err
+    assert " planes launches=" in err, err
+    vkt.synchronize()
+    ref = oracle.brick_decompose(src, brick, ghost)
+    assert len(got) == len(ref)
+    for i, (g, r) in enumerate(zip(got, ref)):
+        g = g.cpu().numpy()
+        assert g.shape == r.shape, i
+        assert np.array_equal(g.view(np.uint8), np.ascontiguousarray(r).view(np.uint8)), f"brick {i}"
+
+
 def test_bricks_of_the_512_volume_reassemble_it():
     """The 512^3 uint8 CT-like volume in 64^3 bricks with 2 ghost cells (the halo a 5^3
     filter needs): interiors reassemble the volume, ghosts match their neighbours."""

@@ -68,6 +68,7 @@ KERNEL_CASES = {
     "tc7_dns512": ("uniform", 2, (512, 512, 256), "random7", "tensor"),
     "direct7_dns512": ("uniform", 2, (512, 512, 256), "random7", "direct"),
     "batch256": None,    # the batching form's 256 volumes (run_batch_case)
+    "bricks2_ct512": None,   # BrickDecompose of the 512^3 volume, 64^3 bricks, 2 ghost cells
 }
 
 # Per-launch DRAM traffic of the kernels this bench reports, from the ncu captures summarised
@@ -988,12 +989,30 @@ def run_batch_case(args):
                                             for d in keep[1::2]))}))
 
 
+def run_bricks_case(args):
+    """BrickDecompose of the step's 512^3 uint8 volume into 64^3 bricks with the 2 ghost cells
+    a 5^3 filter needs, --reps calls, for profiler captures of the brick kernel."""
+    import torch
+    import paper_2203_10213_gb300 as vkt
+    src = torch.from_numpy(workload_host()).cuda()
+    bricks = None
+    for _ in range(args.reps):
+        bricks = vkt.brick_decompose(src, (64, 64, 64), 2)
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    print(json.dumps({"kernel_case": "bricks2_ct512", "reps": args.reps, "bricks": len(bricks),
+                      "checksum": float(sum(float(b.double().mean()) for b in bricks))}))
+
+
 def run_kernel_case(args):
     import torch
     import synth
     import paper_2203_10213_gb300 as vkt
     if args.kernel_case == "batch256":
         run_batch_case(args)
+        return
+    if args.kernel_case == "bricks2_ct512":
+        run_bricks_case(args)
         return
     kind, fmt, dims, filt, path = KERNEL_CASES[args.kernel_case]
     if kind == "uniform":

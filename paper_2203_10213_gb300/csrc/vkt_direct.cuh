@@ -32,7 +32,9 @@
 // Compensated mode (COMP, integer destinations whose FP32 error bound could flip a code):
 // every tap is added as an error-free product and sum (dot2_exact, the compensated dot
 // product Dot2), each output keeps a (sum, error) pair, and the store takes the rounding
-// decision on the pair in double-float arithmetic (comp_code).  One output row per thread
+// decision on the pair in double-float arithmetic (comp_code).  A slot's first tap in a
+// plane of its z-march sets the pair to the product and its rounding error (dot2_first_exact),
+// which is what the addition to (0, 0) gives, so no slot is reset.  One output row per thread
 // keeps the 2 x k x RX accumulators in registers.
 #pragma once
 
@@ -300,9 +302,15 @@ __global__ void __launch_bounds__(NT)
 #pragma unroll
                         for (int x = 0; x < RX; ++x)
 #pragma unroll
-                            for (int a = 0; a < K; ++a)
-                                dot2_exact(W.w[(c * K + b) * K + a], win[x + a], cs[sl][i][x],
-                                           cc[sl][i][x]);
+                            for (int a = 0; a < K; ++a) {
+                                // a slot's first tap in its z-march sets it (no reset needed)
+                                if (c == 0 && b == 0 && a == 0)
+                                    dot2_first_exact(W.w[(c * K + b) * K + a], win[x + a],
+                                                     cs[sl][i][x], cc[sl][i][x]);
+                                else
+                                    dot2_exact(W.w[(c * K + b) * K + a], win[x + a], cs[sl][i][x],
+                                               cc[sl][i][x]);
+                            }
                     } else if constexpr (Cfg::PAIR) {
 #pragma unroll
                         for (int x = 0; x < RX; x += 2)
@@ -364,15 +372,6 @@ __global__ void __launch_bounds__(NT)
                             cc[q][i][x] = cc[q + 1][i][x];
                         }
             }
-            // the slot that starts a new output plane starts from zero
-            constexpr int fresh = Cfg::ROT ? K - 1 : 0;
-#pragma unroll
-            for (int i = 0; i < RY; ++i)
-#pragma unroll
-                for (int x = 0; x < RX; ++x) {
-                    cs[Cfg::ROT ? fresh : sl0][i][x] = 0.f;
-                    cc[Cfg::ROT ? fresh : sl0][i][x] = 0.f;
-                }
             return;
         }
         if (it >= 2 * R) {

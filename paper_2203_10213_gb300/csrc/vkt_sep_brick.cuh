@@ -641,9 +641,10 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
                 load_row<4 + K - 1, 4>(F + row * FP + 4 * g, win);
 #pragma unroll
                 for (int x = 0; x < 4; ++x) {
-                    float hs = 0.f, hc = 0.f;
+                    float hs, hc;
+                    dot2_first_exact(G.gx[0], win[x], hs, hc);
 #pragma unroll
-                    for (int a = 0; a < K; ++a) dot2_step(G.gx[a], win[x + a], 0.f, hs, hc);
+                    for (int a = 1; a < K; ++a) dot2_exact(G.gx[a], win[x + a], hs, hc);
                     T1[row * TX + 4 * g + x] = make_float2(hs, hc);
                 }
             }
@@ -657,14 +658,15 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
         // y pass on the (hi, lo) pairs, then the z pass into the K rotating pair accumulators
         float ts[RX], tc[RX];
 #pragma unroll
-        for (int x = 0; x < RX; ++x) ts[x] = tc[x] = 0.f;
-#pragma unroll
         for (int b = 0; b < K; ++b) {
             const float2* r = T1 + (ty + b) * TX + tx * RX;
 #pragma unroll
             for (int x = 0; x < RX; ++x) {
                 const float2 v = r[x];
-                dot2_step(G.gy[b], v.x, v.y, ts[x], tc[x]);
+                if (b == 0)
+                    dot2_first(G.gy[b], v.x, v.y, ts[x], tc[x]);
+                else
+                    dot2_step(G.gy[b], v.x, v.y, ts[x], tc[x]);
             }
         }
         // z pass: slot K-1-c holds the output plane that this input plane reaches through
@@ -672,8 +674,14 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
 #pragma unroll
         for (int c = 0; c < K; ++c) {
             const int sl = K - 1 - c;
+            // slot K-1 starts a new output plane: its first term sets it (no reset needed)
 #pragma unroll
-            for (int x = 0; x < RX; ++x) dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
+            for (int x = 0; x < RX; ++x) {
+                if (c == 0)
+                    dot2_first(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
+                else
+                    dot2_step(G.gz[c], ts[x], tc[x], acc_s[sl][x], acc_c[sl][x]);
+            }
         }
         constexpr int sl0 = 0;
         if (it >= 2 * R && oy < yend && nvalid > 0) {
@@ -698,8 +706,6 @@ __device__ __forceinline__ bool brick_comp(const Job& J, const Wt& G, const CUte
                 acc_s[q][x] = acc_s[q + 1][x];
                 acc_c[q][x] = acc_c[q + 1][x];
             }
-#pragma unroll
-        for (int x = 0; x < RX; ++x) acc_s[K - 1][x] = acc_c[K - 1][x] = 0.f;
     };
 
     // one plane body, not unrolled: the Dot2 arithmetic of a plane is large, and a loop

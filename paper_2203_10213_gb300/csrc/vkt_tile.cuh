@@ -493,6 +493,21 @@ __device__ __forceinline__ void dot2_exact(float g, float h, float& s, float& c)
     c = __fadd_rn(c, __fadd_rn(t, e));
 }
 
+// (s, c) = g * (h + l) as the first term of a sum: exactly what dot2_step gives from
+// s = c = 0 (TwoSum(0, p) is (p, 0)), without the addition
+__device__ __forceinline__ void dot2_first(float g, float h, float l, float& s, float& c)
+{
+    s = __fmul_rn(g, h);
+    c = __fmaf_rn(g, l, __fmaf_rn(g, h, -s));
+}
+
+// the same for an exact input h (what dot2_exact gives from s = c = 0)
+__device__ __forceinline__ void dot2_first_exact(float g, float h, float& s, float& c)
+{
+    s = __fmul_rn(g, h);
+    c = __fmaf_rn(g, h, -s);
+}
+
 // code = clamp(round-half-even(a0 + a1 * (s + c)), 0, qmax) with a0 = a0h + a0l and
 // a1 = a1h + a1l double-float constants: the product and the sum are formed with their
 // rounding errors, and the rounding decision is taken on the pair (u, lo)

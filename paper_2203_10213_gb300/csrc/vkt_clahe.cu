@@ -204,6 +204,8 @@ __device__ __forceinline__ void cell_range(int i, int s, int nb, int n, int& lo,
     hi = i + 1 < nb ? min(n, s * (i + 1) + s / 2) : n;
 }
 
+// Off: the type of voxel offsets (32 bits for volumes under 2^32 voxels)
+template <typename Off>
 __global__ void __launch_bounds__(NT, 4) k_clahe_map_cells(const uint8_t* __restrict__ src, ClaheGeo g,
                                                         const uint8_t* __restrict__ luts,
                                                         uint8_t* __restrict__ dst, int tz)
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(NT, 4) k_clahe_map_cells(const uint8_t* __rest
             float wz;
             brick_coord(z, g.sz, g.nbz, isz, z0, z1, wz);
             const bool zm = xm && z0 == bz0 && z1 == bz1;
-            const int64_t plane = static_cast<int64_t>(z) * g.ny;
+            const Off plane = static_cast<Off>(z) * g.ny;
             for (int yb = Y0 + warp * RU; yb < Y1; yb += NWARP * RU) {
                 int qv[RU];
 #pragma unroll
@@ -382,7 +384,10 @@ extern "C" vktError vktClahe3DSV(vktStructuredVolume dst, vktStructuredVolume sr
     if (by_cells) {
         const int tz = std::max(1, 16384 / (g.sx * g.sy));
         const dim3 grid(static_cast<unsigned>(cells), (g.sz + tz - 1) / tz);
-        k_clahe_map_cells<<<grid, NT, 0, ctx.stream>>>(s, g, luts, static_cast<uint8_t*>(dst->data), tz);
+        if (bytes <= 0xffffffffull)
+            k_clahe_map_cells<uint32_t><<<grid, NT, 0, ctx.stream>>>(s, g, luts, static_cast<uint8_t*>(dst->data), tz);
+        else
+            k_clahe_map_cells<int64_t><<<grid, NT, 0, ctx.stream>>>(s, g, luts, static_cast<uint8_t*>(dst->data), tz);
     } else {
         const dim3 grid((g.nx + NT - 1) / NT, g.ny, g.nz);
         k_clahe_map<<<grid, NT, 0, ctx.stream>>>(s, g, luts, static_cast<uint8_t*>(dst->data));

@@ -5,11 +5,13 @@
 // s = min(b, dims - o) per axis, and is stored as a volume of s + 2 g voxels per axis whose
 // voxel (i, j, k) is the source voxel clamp(o - g + (i, j, k)): ghost cells inside the volume
 // copy the neighbouring bricks' voxels, ghost cells beyond a face repeat the face voxel (the
-// clamp-to-edge rule of ApplyFilter).  One launch copies every brick: a CTA takes a run of
-// brick rows.  With a 16-byte aligned source and 4-byte aligned bricks (every torch
+// clamp-to-edge rule of ApplyFilter).  One launch copies every brick.  Bricks with ghost
+// cells on a source a tensor map describes take brick planes as the unit (k_bricks_planes:
+// one TMA box per plane, one funnel shift per output word); otherwise a CTA takes a run of
+// brick rows: with a 16-byte aligned source and 4-byte aligned bricks (every torch
 // allocation) the rows are staged in shared memory by asynchronous 16-byte copies and
-// written as blocks or words (k_bricks_staged); otherwise a warp copies four rows at a
-// time, its lanes consecutive x (k_bricks).
+// written as blocks or words (k_bricks_staged), else a warp copies four rows at a time, its
+// lanes consecutive x (k_bricks).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>

@@ -658,6 +658,10 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
         if (job.roi && a.use_tma && job.dfmt == FMT_F32 && job.sfmt == FMT_F32)
             kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, true, false, SHAPE>;
     }
+    if constexpr (ADJ && K >= 3 && K <= 5) {
+        // the adjoint reads and writes float32: formats compiled in for tensor-map jobs
+        if (a.use_tma) kern = k_direct<K, ADJ, FMT_F32, FMT_F32, LM_TMA, false, false, SHAPE>;
+    }
     if constexpr (!ADJ && !COMP && K >= 3 && K <= 5) {
         if (!job.roi && job.dfmt == FMT_F32 && job.sfmt == FMT_U8) {
             if (a.use_tma) kern = k_direct<K, ADJ, FMT_U8, FMT_F32, LM_TMA, false, false, SHAPE>;

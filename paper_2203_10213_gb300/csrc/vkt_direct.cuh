@@ -40,6 +40,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "vkt_internal.h"
 #include "vkt_tile.cuh"
@@ -446,6 +447,39 @@ __global__ void __launch_bounds__(NT)
 // 8 x 128^3, k = 5: the x slabs' loads hit a different row in every lane.)
 constexpr int SHELL_T = 16;   // output tile edge of the shell kernel (256 threads)
 
+// The folded weights of the shell [face: low, high][axis: z, y, x][t][u][v] (t the layer of
+// the folded axis, (u, v) the other two taps in (c, b, a) order), summed in float32 on the
+// host in tap order and passed as launch constants, so the kernel's FMAs take them as
+// constant operands.
+template <int K>
+struct ShellW {
+    static constexpr int R = (K - 1) / 2;
+    static constexpr int RKK = R > 0 ? R * K * K : 1;
+    float f[6][RKK];
+};
+
+template <int K>
+ShellW<K> fold_shell_weights(const DenseW<K>& W)
+{
+    constexpr int R = (K - 1) / 2, KK = K * K;
+    ShellW<K> F;
+    for (int face = 0; face < 2; ++face)
+        for (int axis = 0; axis < 3; ++axis)
+            for (int q = 0; q < R * KK; ++q) {
+                const int t = q / KK, u = (q / K) % K, v = q % K;
+                const int f0 = face == 0 ? t + R + 1 : 0, f1 = face == 0 ? 2 * R : t;
+                float sum = 0.f;
+                for (int f = f0; f <= f1; ++f) {
+                    const int c = axis == 0 ? f : u;
+                    const int b = axis == 0 ? u : (axis == 1 ? f : v);
+                    const int a = axis == 2 ? f : v;
+                    sum += W.w[(c * K + b) * K + a];
+                }
+                F.f[face * 3 + axis][q] = sum;
+            }
+    return F;
+}
+
 template <int K>
 __host__ __device__ constexpr int shell_tiles(int nx, int ny, int nz, int* na, int* nb)
 {
@@ -462,27 +496,11 @@ __host__ __device__ constexpr int shell_tiles(int nx, int ny, int nz, int* na, i
 template <int K>
 __global__ void __launch_bounds__(SHELL_T * SHELL_T)
     k_adjoint_shell(const float* __restrict__ gy, float* gx, int nx, int ny, int nz,
-                    int64_t vs_src, int64_t vs_dst, const DenseW<K> W)
+                    int64_t vs_src, int64_t vs_dst, const ShellW<K> FW)
 {
-    constexpr int R = (K - 1) / 2, KK = K * K, RKK = R * K * K, T = SHELL_T, SP = T + 2 * R;
-    // folded weights [face: low, high][axis: z, y, x][t][u][v]: t the layer of the folded
-    // axis, (u, v) the other two taps in (c, b, a) order
-    __shared__ float fw[2][3][RKK];
+    constexpr int R = (K - 1) / 2, T = SHELL_T, SP = T + 2 * R;
     __shared__ float S[R][SP][SP];
     const int tid = threadIdx.x;
-    for (int e = tid; e < 6 * RKK; e += T * T) {
-        const int face = e / (3 * RKK), axis = (e / RKK) % 3, q = e % RKK;
-        const int t = q / KK, u = (q / K) % K, v = q % K;
-        const int f0 = face == 0 ? t + R + 1 : 0, f1 = face == 0 ? 2 * R : t;
-        float sum = 0.f;
-        for (int f = f0; f <= f1; ++f) {
-            const int c = axis == 0 ? f : u;
-            const int b = axis == 0 ? u : (axis == 1 ? f : v);
-            const int a = axis == 2 ? f : v;
-            sum += W.w[(c * K + b) * K + a];
-        }
-        fw[face][axis][q] = sum;
-    }
     // programmatic launch: the main adjoint launch's stores are complete and visible
     grid_dependency_wait();
     launch_dependents();
@@ -533,14 +551,26 @@ __global__ void __launch_bounds__(SHELL_T * SHELL_T)
     const int tx = tid % T, ty = tid / T;
     const int p = p0 + ty, q = q0 + tx;
     if (p >= P || q >= Q) return;
-    const float* f = fw[face][slab];
+    // the (face, slab) weights as compile-time indices of the launch constants
     float acc = 0.f;
+    auto fold = [&](auto fs) {
+        constexpr int FS = decltype(fs)::value;
 #pragma unroll
-    for (int t = 0; t < R; ++t)
+        for (int t = 0; t < R; ++t)
 #pragma unroll
-        for (int u = 0; u < K; ++u)
+            for (int u = 0; u < K; ++u)
 #pragma unroll
-            for (int v = 0; v < K; ++v) acc = fmaf(f[(t * K + u) * K + v], S[t][ty + u][tx + v], acc);
+                for (int v = 0; v < K; ++v)
+                    acc = fmaf(FW.f[FS][(t * K + u) * K + v], S[t][ty + u][tx + v], acc);
+    };
+    switch (face * 3 + slab) {
+    case 0: fold(std::integral_constant<int, 0>{}); break;
+    case 1: fold(std::integral_constant<int, 1>{}); break;
+    case 2: fold(std::integral_constant<int, 2>{}); break;
+    case 3: fold(std::integral_constant<int, 3>{}); break;
+    case 4: fold(std::integral_constant<int, 4>{}); break;
+    default: fold(std::integral_constant<int, 5>{}); break;
+    }
     int ox, oy, oz;
     if (slab == 0) {
         ox = clampi(q - R, 0, nx - 1); oy = clampi(p - R, 0, ny - 1); oz = face == 0 ? 0 : nz - 1;
@@ -701,7 +731,7 @@ vktError launch_k(const Job& job, const float* w, const Ctx& ctx)
             const int tiles = shell_tiles<K>(job.nx, job.ny, job.nz, nullptr, nullptr);
             e = launch_pdl(k_adjoint_shell<K>, dim3(tiles, nv), dim3(SHELL_T * SHELL_T), 0, ctx.stream,
                            static_cast<const float*>(a.src), static_cast<float*>(a.dst), job.nx,
-                           job.ny, job.nz, a0.vs_src, a0.vs_dst, W);
+                           job.ny, job.nz, a0.vs_src, a0.vs_dst, fold_shell_weights<K>(W));
             count_launches(1);
             if (e == cudaSuccess) e = cudaGetLastError();
             if (e != cudaSuccess) return from_cuda(e);

@@ -69,6 +69,8 @@ KERNEL_CASES = {
     "direct7_dns512": ("uniform", 2, (512, 512, 256), "random7", "direct"),
     "batch256": None,    # the batching form's 256 volumes (run_batch_case)
     "bricks2_ct512": None,   # BrickDecompose of the 512^3 volume, 64^3 bricks, 2 ghost cells
+    "render_ct512": None,    # the render form's 1024 x 768 frame of the 512^3 volume
+    "backward_train": None,  # the differentiation form's batch backward (8 x 128^3, k = 5)
 }
 
 # Per-launch DRAM traffic of the kernels this bench reports, from the ncu captures summarised
@@ -1004,6 +1006,51 @@ def run_bricks_case(args):
                       "checksum": float(sum(float(b.double().mean()) for b in bricks))}))
 
 
+def run_render_case(args):
+    """The render form's frame (1024 x 768 of the 512^3 uint8 volume, step 0.5), --reps calls,
+    for profiler captures of the ray-marching kernel."""
+    import torch
+    import paper_2203_10213_gb300 as vkt
+    src = torch.from_numpy(workload_host()).cuda()
+    img = None
+    for _ in range(args.reps):
+        img = vkt.render(src, 1024, 768, (256, 300, -600), (256, 256, 256), (0, 1, 0), 0.8, 0.5,
+                         [[0, 0, 0, 0], [1, 0.8, 0.5, 0.1], [1, 1, 1, 0.6]])
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    print(json.dumps({"kernel_case": "render_ct512", "reps": args.reps,
+                      "checksum": float(img.double().mean())}))
+
+
+def run_backward_case(args):
+    """The differentiation form's batch backward (8 float32 blob volumes of 128^3, dense 5^3
+    kernel N(0, 0.1)), --reps calls, for profiler captures of the adjoint, shell and
+    weight-gradient kernels."""
+    import ctypes
+    import torch
+    import synth
+    import paper_2203_10213_gb300 as vkt
+    B, n, k = 8, 128, 5
+    x = torch.from_numpy(np.stack([synth.blobs(synth.BASE_SEED + 100 + b, (n, n, n))
+                                   for b in range(B)]).astype(np.float32)).cuda()
+    f = vkt.Filter.dense(synth.normal(synth.BASE_SEED + 200, (k, k, k), 0.0, 0.1).astype(np.float32))
+    gy = x * 1e-3
+    gx = torch.zeros_like(x)
+    gw = torch.zeros(k ** 3, dtype=torch.float32, device="cuda")
+    vx = [vkt.StructuredVolume.from_tensor(x[b]) for b in range(B)]
+    vgx = [vkt.StructuredVolume.from_tensor(gx[b]) for b in range(B)]
+    vgy = [vkt.StructuredVolume.from_tensor(gy[b]) for b in range(B)]
+    arr = ctypes.c_void_p * B
+    hx, hgx, hgy = (arr(*(v.handle.value for v in vs)) for vs in (vx, vgx, vgy))
+    with vkt.policy(path="direct"):
+        for _ in range(args.reps):
+            vkt.check(vkt._lib.vktApplyFilterBackwardBatchSV(B, hgx, ctypes.c_void_p(gw.data_ptr()),
+                                                            hgy, hx, f.handle))
+    torch.cuda.synchronize()
+    vkt.synchronize()
+    print(json.dumps({"kernel_case": "backward_train", "reps": args.reps, "gw0": float(gw[0])}))
+
+
 def run_kernel_case(args):
     import torch
     import synth
@@ -1013,6 +1060,12 @@ def run_kernel_case(args):
         return
     if args.kernel_case == "bricks2_ct512":
         run_bricks_case(args)
+        return
+    if args.kernel_case == "render_ct512":
+        run_render_case(args)
+        return
+    if args.kernel_case == "backward_train":
+        run_backward_case(args)
         return
     kind, fmt, dims, filt, path = KERNEL_CASES[args.kernel_case]
     if kind == "uniform":

@@ -59,6 +59,9 @@ def test_bricks_match_oracle(fmt, shape, brick, ghost):
     (synth.F32, (21, 22, 28), (12, 8, 8), 3),     # partial last brick along x
     (synth.F32, (13, 9, 32), (4, 4, 5), 4),
     (synth.F32, (8, 6, 16), (4, 3, 2), 1),
+    (synth.U8, (10, 12, 16), (32, 4, 4), 2),      # bricks wider than the volume: the box
+    (synth.U16, (6, 9, 8), (16, 16, 3), 3),       # reaches past it (zero-filled, never read)
+    (synth.F32, (5, 7, 4), (8, 8, 8), 1),
 ])
 def test_plane_image_kernel(fmt, shape, brick, ghost, capfd):
     """Ghost cells on a source a tensor map describes, brick widths of whole 16-byte blocks
